@@ -1,0 +1,24 @@
+"""Plain FP64 CPU oracle of the coupled pseudopotential-flow + improved thermal MRT-LB step.
+
+TEST INFRASTRUCTURE ONLY. This package is the slow, obviously correct statement of what the
+GPU library computes, written from Li, Zhou & Yan, "Improved thermal lattice Boltzmann model
+for simulation of liquid-vapor phase change" (arXiv:1709.04400). Only the tests, the smoke
+check in ``__graft_entry__`` and the CPU-baseline / reference arm of ``bench.py`` may import
+it. The GPU library never imports, links or calls anything here, and nothing here imports the
+GPU library: the two share no code. Inputs come from ``paper_1709_04400_gb300.inputs``, a
+module that holds random-number and initial-shape generation only.
+
+Modules
+-------
+lattice  D2Q9 velocities, weights and the MRT transformation matrix (Eqs. 42-44).
+eos      Peng-Robinson equation of state (Eq. 56), (dp/dT)_rho, psi, Maxwell coexistence.
+model    The time step, whole-array passes in the order the paper states the model
+         (Sec. III B summary after Eq. 55; Eqs. 45-47, 53-55; Eq. 28 source).
+
+Every function cites the passage it follows. Where the paper delegates a detail to a reference
+that is not reproduced in the paper (flow model, isotropic stencils, Zou-He, contact angle),
+the reading taken is stated in the docstring and marked READING.
+"""
+
+from . import lattice, eos, model  # noqa: F401
+from .model import OracleParams, OracleState, OracleNonPhysical, init_state, step, run, fields  # noqa: F401

@@ -1,0 +1,130 @@
+"""Physics pins of the oracle (the five references the coupled method must reproduce):
+mass conservation (test_oracle_invariants), the analytic chi q^2 decay of a temperature mode,
+the Chapman-Enskog prediction for advected heat (improved vs compromised model), the Laplace law,
+EOS-consistent coexistence of a flat interface and the D^2 law of droplet evaporation."""
+
+import numpy as np
+import pytest
+
+from oracle import eos, model
+from paper_1709_04400_gb300 import inputs
+
+A, B, R, OM = 3.0 / 49.0, 2.0 / 21.0, 1.0, 0.344
+TC = eos.critical_temperature(A, B, R)
+TS = 0.86 * TC
+RV, RL, _ = eos.maxwell_coexistence(TS, A, B, R, OM)
+SG = (1.0, 1.0, 1.0, 1.0, 1.2, 1.0, 1.2, 1.0, 1.0)
+
+
+def _decay_rate(N, rho0):
+    """Fitted decay rate of T = T0 + eps sin(q x) in a uniform fluid at rest."""
+    q = 2 * np.pi / N
+    chi = (2.0 / 3.0) / (rho0 * 5.0)
+    p = model.OracleParams(nx=N, ny=4, s_g=SG, frozen_flow=(0.0, 0.0))
+    x = np.arange(N)[None, :] * np.ones((4, 1))
+    s = model.init_state(p, np.full((4, N), rho0), TS + 1e-3 * np.sin(q * x))
+    ts, amp = [], []
+    for _ in range(int(3 / (chi * q * q))):
+        s = model.step(p, s)
+        if s.step >= 10 and s.step % 5 == 0:
+            ts.append(s.step)
+            amp.append(2.0 / N * ((s.g.sum(0)[0] - TS) * np.sin(q * x[0])).sum())
+    return -np.polyfit(ts, np.log(amp), 1)[0], chi * q * q
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("rho0", [2.0, 0.5])  # chi = lambda/(rho c_V) below and above k = 1/6
+def test_chi_q2_decay(rho0):
+    """Eq. 5 with v = 0 and uniform rho is dT/dt = chi lap T, chi = lambda/(rho c_V): a Fourier mode
+    decays as exp(-chi q^2 t). The LB diffusivity k and the source's (chi - k) lap T must add up to
+    chi, and the error must fall at second order."""
+    r32, e32 = _decay_rate(32, rho0)
+    r64, e64 = _decay_rate(64, rho0)
+    err32, err64 = abs(r32 / e32 - 1), abs(r64 / e64 - 1)
+    assert err64 < 0.006
+    assert 3.5 < err32 / err64 < 4.5
+
+
+def _advect(mdl, v0=0.1, nsteps=300):
+    N, rho0, s0, x0 = 128, 2.0, 4.0, 40.0
+    p = model.OracleParams(nx=N, ny=4, s_g=SG, frozen_flow=(v0, 0.0), model=mdl)
+    x = np.arange(N)[None, :] * np.ones((4, 1))
+    s = model.init_state(p, np.full((4, N), rho0), TS + 1e-3 * np.exp(-((x - x0) ** 2) / (2 * s0 * s0)))
+    s = model.run(p, s, nsteps)
+    d = s.g.sum(0)[0] - TS
+    xx = np.arange(N)
+    c = (d * xx).sum() / d.sum()
+    var = (d * (xx - c) ** 2).sum() / d.sum()
+    chi = (2.0 / 3.0) / (rho0 * 5.0)
+    return c, (var - s0 * s0) / (2 * chi * nsteps), x0 + v0 * nsteps
+
+
+@pytest.mark.slow
+def test_advection_error_term_removed():
+    """A Gaussian heat pulse in a uniform flow v0 spreads with chi in the improved model (Eq. 41/A22),
+    while the compromised model (no Eqs. 54-55) carries the error term div[eta d_t0(T v)] of Eq. A12,
+    i.e. an extra diffusivity -eta v0^2 along the flow, eta = 1/s3 - 1/2 (Eq. A13)."""
+    c_i, ratio_i, c_exp = _advect("improved")
+    c_c, ratio_c, _ = _advect("compromised")
+    assert abs(c_i - c_exp) < 0.1 and abs(c_c - c_exp) < 0.1
+    assert abs(ratio_i - 1) < 0.005
+    eta, v0, chi = 0.5, 0.1, (2.0 / 3.0) / 10.0
+    assert abs((ratio_c - 1) - (-eta * v0 * v0 / chi)) < 0.005
+
+
+@pytest.mark.slow
+def test_laplace_law():
+    """North-star reference 3: static droplets, isothermal; p_in - p_out is linear in 1/R with a
+    vanishing intercept."""
+    N = 64
+    res = []
+    for Rd in (10, 13, 16):
+        p = model.OracleParams(nx=N, ny=N, frozen_thermal=True)
+        rho = inputs.tanh_droplet(N, N, Rd, 4, RL, RV)
+        s = model.run(p, model.init_state(p, rho, np.full((N, N), TS)), 2500)
+        r = s.last["rho"]
+        res.append((Rd, eos.pressure(r[N // 2, N // 2], TS, A, B, R, OM) - eos.pressure(r[0, 0], TS, A, B, R, OM)))
+    x = 1.0 / np.array([r for r, _ in res])
+    y = np.array([d for _, d in res])
+    c = np.polyfit(x, y, 1)
+    r2 = 1 - ((y - np.polyval(c, x)) ** 2).sum() / ((y - y.mean()) ** 2).sum()
+    assert c[0] > 0 and r2 > 0.99
+    assert abs(c[1]) < 0.1 * y.min()
+
+
+@pytest.mark.slow
+def test_flat_interface_coexistence():
+    """North-star reference 4: a periodic liquid slab reaches plateau densities close to the Maxwell
+    coexistence values of Eq. 56 at T_sat = 0.86 T_c (the sigma term tunes this; pseudopotential
+    models are not exactly thermodynamically consistent)."""
+    p = model.OracleParams(nx=4, ny=128, frozen_thermal=True)
+    rho = inputs.tanh_layer(4, 128, 64, 4, RL, RV)
+    rho = np.where(np.arange(128)[:, None] < 32, inputs.tanh_layer(4, 128, 32, 4, RV, RL), rho)
+    s = model.run(p, model.init_state(p, rho, np.full_like(rho, TS)), 5000)
+    col = s.last["rho"][:, 0]
+    assert abs(col[48] / RL - 1) < 0.005
+    assert abs(col[0] / RV - 1) < 0.04
+
+
+@pytest.mark.slow
+def test_d2_law():
+    """North-star reference 5 (Sec. IV A, Fig. 2): a droplet at T_sat in superheated surroundings
+    evaporates with (D/D0)^2 linear in time after the initial transient."""
+    N, Rd, dT = 64, 14.0, 0.3 * TC
+    p = model.OracleParams(nx=N, ny=N, t_bc=("dirichlet",) * 4, T_bc=(TS + dT,) * 4)
+    rho, T = inputs.droplet_hot_ring(N, N, Rd, 4, RL, RV, TS, dT)
+    s = model.init_state(p, rho, T)
+    ts, area = [], []
+    for _ in range(24):
+        s = model.run(p, s, 250)
+        r = s.last["rho"]
+        lo = np.mean([r[2, 2], r[2, -3], r[-3, 2], r[-3, -3]])
+        hi = r[N // 2, N // 2]
+        ts.append(s.step)
+        area.append(np.clip((r - lo) / (hi - lo), 0, 1).sum())
+    ts, d2 = np.array(ts), np.array(area) / area[0]
+    m = ts >= 1500
+    c = np.polyfit(ts[m], d2[m], 1)
+    r2 = 1 - ((d2[m] - np.polyval(c, ts[m])) ** 2).sum() / ((d2[m] - d2[m].mean()) ** 2).sum()
+    assert c[0] < 0 and r2 > 0.99
+    assert d2[-1] < 0.95
