@@ -127,14 +127,16 @@ def heat_meq(T, vx, vy, model):
 
 
 def init_state(p: OracleParams, rho, T, ux=None, uy=None) -> OracleState:
-    """Initial populations f = M^{-1} m_eq(rho, u), g = M^{-1} m_eq(T, u) (equilibrium start)."""
+    """Initial populations f = M^{-1} m_eq(rho, u), g = M^{-1} m_eq(T, u) (equilibrium start),
+    closed once by the boundary step so that the state, like every later one, holds post-boundary
+    populations (READING: the paper does not state how the initial state meets the boundaries)."""
     p.check()
     rho = np.asarray(rho, dtype=np.float64).reshape(p.ny, p.nx)
     T = np.asarray(T, dtype=np.float64).reshape(p.ny, p.nx)
     ux = np.zeros_like(rho) if ux is None else np.asarray(ux, dtype=np.float64).reshape(p.ny, p.nx)
     uy = np.zeros_like(rho) if uy is None else np.asarray(uy, dtype=np.float64).reshape(p.ny, p.nx)
-    f = L.from_moments(flow_meq(rho, ux, uy))
-    g = L.from_moments(heat_meq(T, ux, uy, p.model))
+    f = flow_boundaries(p, L.from_moments(flow_meq(rho, ux, uy)))
+    g = heat_boundaries(p, L.from_moments(heat_meq(T, ux, uy, p.model)))
     return OracleState(f=f, g=g, phi_prev=None, rho_ave=float(np.mean(f.sum(axis=0))))
 
 
