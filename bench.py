@@ -1,0 +1,338 @@
+"""Benchmark of the coupled flow + thermal lattice Boltzmann step on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+                    [--workload evaporation|droplet|heated_wall] [--n SIDE] [--prec fp64|fp32]
+
+A bench step is one coupled time step (flow and thermal populations, every part of the hot path)
+over the whole grid. Default workload: 256 x 256 droplet evaporation (R = 40, dT = 0.1 T_c,
+Sec. IV A set-up), FP64 storage and arithmetic. Metric: coupled MLUPS (million lattice-node updates
+of f and g per second). The working set of 256^2 is smaller than L2, so L2 is flushed (a 512 MiB
+write) before every timed step and each step is timed with CUDA events on the library's stream.
+
+Under torchrun (N > 1) each rank advances its own independent replica (weak scaling, no collective
+on the data path); value = all ranks' node updates / the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle on the same workload, one oracle step per bench step, on
+rank 0 only.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="evaporation", choices=["evaporation", "droplet", "heated_wall"])
+    ap.add_argument("--n", type=int, default=0, help="grid side (0 = the workload's own size)")
+    ap.add_argument("--dT", type=float, default=0.1, help="superheat dT / T_c of the evaporation case")
+    ap.add_argument("--prec", default="", choices=["", "fp64", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_case(args, Tc, rv, rl):
+    from paper_1709_04400_gb300 import workloads
+
+    if args.workload == "evaporation":
+        n = args.n or 256
+        case, rho, T = workloads.droplet_evaporation(Tc, rv, rl, n=n, radius=40.0 * n / 256, dT_ratio=args.dT)
+        prec = args.prec or "fp64"
+    elif args.workload == "droplet":
+        n = args.n or 128
+        case, rho, T = workloads.droplet_periodic(Tc, rv, rl, n=n, radius=25.0 * n / 128)
+        prec = args.prec or "fp64"
+    else:
+        case, rho, T = workloads.heated_wall(Tc, rv, rl)
+        prec = args.prec or "fp32"
+    return case, rho, T, prec
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(case, rho, T, budget_s=12.0):
+    """The FP64 oracle as it stands, on this host, on the bench workload for a bounded number of steps."""
+    from oracle import model
+
+    keys = set(model.OracleParams.__dataclass_fields__)
+    p = model.OracleParams(**{k: v for k, v in case.items() if k in keys})
+    s = model.init_state(p, rho, T)
+    s = model.step(p, s)  # warm-up
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        s = model.step(p, s)
+        n += 1
+    dt = time.perf_counter() - t0
+    N = case["nx"] * case["ny"]
+    return {"value": N * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{n} oracle steps of the {case['nx']}x{case['ny']} workload ({dt:.1f} s, numpy FP64, 1 thread)"}
+
+
+# Algorithmic traffic of the collide kernel per node: pull 9 f + 9 g, write 9 f* + 9 g*, read/write
+# phi_prev, read the centre of 8 scratch planes (rho, T, vx, vy, Fx, Fy, Q, dp/dT); the neighbour
+# reads of T, vx, vy (and rho) are served by L1/L2 and not counted.
+def collide_bytes_per_node(prec_bytes, lambda_rho):
+    planes = 8 + (0 if not lambda_rho else 0)
+    return prec_bytes * (18 + 18 + 2 + planes)
+
+
+# Algorithmic FP64 operations of the collide kernel per node (each add, subtract, multiply, divide and
+# square root counted once; an FMA counts as its multiply and its add). Counted from the kernel
+# source, term by term; see the design notes for the breakdown.
+COLLIDE_FLOPS = {"const": 345, "rho_cv_chi": 366}
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1709_04400_gb300 import build, lbpc
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    build.build()
+    p0 = lbpc.Params(nx=8, ny=8)
+    Tc, _ = lbpc.eos_critical(p0)
+    rv, rl, _ = lbpc.coexistence(p0, 0.86 * Tc)
+    case, rho, T, prec_name = make_case(args, Tc, rv, rl)
+    prec = lbpc.FP64 if prec_name == "fp64" else lbpc.FP32
+    params = lbpc.params_from_case(case, prec)
+    N = case["nx"] * case["ny"]
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    sim = lbpc.Simulation(params)
+    sim.init(rho, T)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    stream = sim.stream
+
+    def one_step():
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        return sim.step_timed()
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    per_kernel = {}
+    step_ms = []
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ks = one_step()
+            step_ms.append(sum(ks.values()))
+            for k, v in ks.items():
+                per_kernel.setdefault(k, []).append(v)
+        torch.cuda.synchronize()
+        barrier()
+        wall = time.perf_counter() - t0
+    clocks = clk.summary()
+    dev_s = sum(step_ms) / 1e3
+    t_all = torch.tensor([dev_s, wall], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
+    dev_s, wall = float(t_all[0]), float(t_all[1])
+    value = ws * N * args.steps / dev_s / 1e6
+    nk = len(per_kernel)
+
+    # dominant kernel and its roofline
+    avg = {k: sum(v) / len(v) for k, v in per_kernel.items()}
+    top = max(avg, key=avg.get)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    if prec == lbpc.FP64:
+        flops = COLLIDE_FLOPS[case["lambda_mode"]] * N
+        achieved = flops / (avg["k_collide"] / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_collide", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
+                "frac": achieved / 1.25, "traffic": None,
+                "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s, profiling recipe)",
+                "top_kernel": top}
+    else:
+        bytes_ = collide_bytes_per_node(4, case["lambda_mode"] == "rho_cv_chi") * N
+        achieved = bytes_ / (avg["k_collide"] / 1e3) / 1e9
+        peak = float(peaks.get("hbm_gbs", 6800.0))
+        roof = {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6.8 TB/s",
+                "top_kernel": top}
+
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the public API with pinned host buffers: H2D of the initial fields,
+        # every step followed by a D2H read of the step's result (domain mass and heat), and the
+        # final fields read back to the host
+        h_rho = torch.from_numpy(np.ascontiguousarray(rho)).pin_memory().numpy()
+        h_T = torch.from_numpy(np.ascontiguousarray(T)).pin_memory().numpy()
+        sim2 = lbpc.Simulation(params)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim2.init(h_rho, h_T)
+        for _ in range(args.steps):
+            sim2.step(1)
+            sim2.sums()
+        out = sim2.fields()
+        torch.cuda.synchronize()
+        barrier()
+        te = time.perf_counter() - t0
+        t_e = torch.tensor([te], dtype=torch.float64, device="cuda")
+        if ws > 1:
+            dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
+        te = float(t_e[0])
+        sim2.close()
+        h2d = 2 * N * 8
+        d2h = args.steps * 16 + 4 * N * 8
+        e2e = {"value": ws * N * args.steps / te / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "note": "lbpc_init from pinned host fields, lbpc_step(1) + lbpc_sums per step, lbpc_fields to host"}
+    sim.close()
+
+    base = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline(case, rho, T)
+
+    if rank == 0:
+        line = {
+            "metric": "coupled flow+thermal MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_s * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == lbpc.FP64 else "f32", "data": "synthetic",
+            "config": {"workload": case["name"], "nx": case["nx"], "ny": case["ny"], "nodes": N,
+                       "storage": prec_name, "parallelism": f"replicas{ws}",
+                       "l2": "flushed before every timed step (512 MiB write); each step timed with CUDA events",
+                       "wall_ms_per_step": wall * 1e3 / args.steps},
+            "roofline": roof, "cpu_baseline": base, "e2e": e2e,
+            "gpu_launches": nk * args.steps,
+            "kernel_ms": {k: sum(v) / len(v) for k, v in per_kernel.items()},
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from oracle import eos, model
+
+    a, b, R, om = 3.0 / 49.0, 2.0 / 21.0, 1.0, 0.344
+    Tc = eos.critical_temperature(a, b, R)
+    rv, rl, _ = eos.maxwell_coexistence(0.86 * Tc, a, b, R, om)
+    case, rho, T, prec_name = make_case(args, Tc, rv, rl)
+    keys = set(model.OracleParams.__dataclass_fields__)
+    p = model.OracleParams(**{k: v for k, v in case.items() if k in keys})
+    s = model.init_state(p, rho, T)
+    for _ in range(args.warmup):
+        s = model.step(p, s)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s = model.step(p, s)
+    dt = time.perf_counter() - t0
+    N = case["nx"] * case["ny"]
+    v = N * args.steps / dt / 1e6
+    sample = f"{args.steps} oracle steps of {case['name']} ({dt:.1f} s, numpy FP64, 1 thread)"
+    line = {"impl": "reference", "metric": "coupled flow+thermal MLUPS", "value": v, "unit": "MLUPS",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": case["name"], "nx": case["nx"], "ny": case["ny"], "nodes": N,
+                       "storage": "fp64", "parallelism": "cpu oracle, rank 0 only"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(var, "1")
+    a = parse()
+    if a.warmup < 3:
+        a.warmup = 3
+    (run_reference if a.impl == "reference" else run_native)(a)

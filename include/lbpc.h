@@ -1,0 +1,172 @@
+/*
+ * lbpc.h - C ABI of liblbpc, the GB300 (sm_103a) implementation of the coupled lattice Boltzmann
+ * time step for liquid-vapor phase change of Li, Zhou & Yan, "Improved thermal lattice Boltzmann
+ * model for simulation of liquid-vapor phase change" (arXiv:1709.04400).
+ *
+ * One step on a 2D D2Q9 grid is: pseudopotential psi from the Peng-Robinson EOS at local (rho, T)
+ * (Eq. 56), the neighbour-sum interaction force, the MRT density collide with forcing plus stream
+ * (the flow model the paper takes from its Refs. [13,29]), and the improved thermal MRT step for T
+ * (Eqs. 45-47 with the equilibria of Eq. 53, the source of Eq. 28 and the corrections of
+ * Eqs. 54-55), with the moment and isotropic-gradient evaluations that feed it.
+ *
+ * Conventions for every function:
+ *   - Lattice units: dt = dx = 1, c_s^2 = 1/3. Fields are row-major [ny][nx] (x fastest), FP64,
+ *     whatever the storage precision of the populations.
+ *   - Every function returns an lbpc_status; nothing throws across the ABI. The first error of a
+ *     context is sticky: later calls that would advance or change the state return LBPC_ESTATE,
+ *     while lbpc_fields, lbpc_sums, lbpc_populations and lbpc_last_error still work.
+ *   - The caller owns every buffer passed in (the device workspace included); the library owns only
+ *     the context struct, which lbpc_destroy frees. The library never allocates device memory.
+ *   - "on_device" = 1: pointers are device pointers (any CUDA allocation of the current device);
+ *     0: host pointers (pageable or pinned), copied through the context's stream.
+ *   - All device work runs on the stream given to lbpc_create.
+ */
+#ifndef LBPC_H
+#define LBPC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBPC_VERSION 1
+
+typedef struct lbpc_ctx lbpc_ctx; /* opaque */
+
+typedef enum {
+  LBPC_OK = 0,
+  LBPC_EINVAL = 1,    /* invalid argument or parameter set */
+  LBPC_ENOMEM = 2,    /* workspace smaller than lbpc_workspace_bytes() */
+  LBPC_ECUDA = 3,     /* a CUDA runtime call failed; lbpc_last_error has its message */
+  LBPC_ENONPHYS = 4,  /* rho <= 0, rho >= 1/b, T <= 0, psi^2 < 0 or non-finite; step, x, y reported */
+  LBPC_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
+  LBPC_ESTATE = 6     /* the context holds an earlier error */
+} lbpc_status;
+
+/* Storage precision of the populations f, g (arithmetic: FP64 for LBPC_FP64, FP32 otherwise). */
+typedef enum { LBPC_FP64 = 0, LBPC_FP32 = 1 } lbpc_prec;
+
+/* Flow boundary of an edge. x edges must be periodic; y edges are both periodic or both not.
+ * A non-periodic y edge is an on-node row closed by the Zou-He scheme (the paper applies Zou-He at
+ * the solid surface, Sec. IV A, citing its Ref. [51]): LBPC_WALL = no-slip wall (u = 0),
+ * LBPC_PRESSURE = fixed density rho_bc with u_x = 0 (the open / fixed-pressure top). */
+typedef enum { LBPC_PERIODIC = 0, LBPC_WALL = 1, LBPC_PRESSURE = 2 } lbpc_flow_bc;
+
+/* Thermal boundary of an edge: LBPC_T_DIRICHLET holds T = T_bc on the edge row/column (the
+ * constant-temperature boundaries of Sec. IV A and IV B). On a non-periodic y edge without a
+ * Dirichlet T the unknown g populations bounce back (zero normal heat flux). */
+typedef enum { LBPC_T_NONE = 0, LBPC_T_DIRICHLET = 1 } lbpc_thermal_bc;
+
+/* Thermal conductivity: constant lambda (Sec. IV A) or lambda = rho c_V chi (Sec. IV A, B), for
+ * which div(lambda grad T) = lambda lap T + grad lambda . grad T. */
+typedef enum { LBPC_LAMBDA_CONST = 0, LBPC_LAMBDA_RHO_CV_CHI = 1 } lbpc_lambda_mode;
+
+/* LBPC_IMPROVED: the paper's model (Eq. 53 equilibria, S0 = phi + 0.5 dt d_t phi, Eqs. 54-55).
+ * LBPC_COMPROMISED: the comparison model of Sec. IV (Eq. 44 equilibria, S0 = phi, no corrections). */
+typedef enum { LBPC_IMPROVED = 0, LBPC_COMPROMISED = 1 } lbpc_thermal_model;
+
+/* Edge order in the arrays below: 0 = x-, 1 = x+, 2 = y- (bottom, y = 0), 3 = y+ (top, y = ny-1). */
+typedef struct {
+  int32_t nx, ny;          /* grid; nx >= 2, ny >= 2 (ny >= 3 with non-periodic y) */
+  int32_t prec;            /* lbpc_prec */
+  int32_t model;           /* lbpc_thermal_model */
+  int32_t lambda_mode;     /* lbpc_lambda_mode */
+  int32_t buoyancy;        /* nonzero: add F_b = (rho - rho_ave) g (Sec. IV B) */
+  int32_t flow_bc[4];      /* lbpc_flow_bc per edge */
+  int32_t t_bc[4];         /* lbpc_thermal_bc per edge */
+  int32_t strip_x0, strip_x1; /* heated strip [x0, x1) on the y- row at T_strip (needs t_bc[2]); x0 = x1: none */
+  double a, b, R, omega;   /* Peng-Robinson EOS, Eq. 56 (paper: 3/49, 2/21, 1, 0.344) */
+  double G;                /* interaction strength of the pseudopotential force (reading: -1) */
+  double s_f[9];           /* flow MRT rates, moments (rho,e,eps,jx,qx,jy,qy,pxx,pxy); s_f[7]=s_f[8]=1/(3 nu+1/2) */
+  double s_g[9];           /* thermal MRT rates (Eq. 43); k = (1/s_g[3] - 1/2)/3 (Eq. 41); s_g[5] = s_g[3] */
+  double sigma;            /* mechanical-stability coefficient of the flow forcing (reading: 0.1) */
+  double lambda;           /* constant thermal conductivity (LBPC_LAMBDA_CONST) */
+  double chi;              /* thermal diffusivity for lambda = rho c_V chi */
+  double cV;               /* specific heat at constant volume */
+  double gx, gy;           /* gravitational acceleration g (Sec. IV B uses g = (0, -g)) */
+  double rho_bc[4];        /* density held on LBPC_PRESSURE edges */
+  double T_bc[4];          /* temperature held on LBPC_T_DIRICHLET edges */
+  double T_strip;          /* temperature of the heated strip */
+  double G_wall;           /* fluid-solid strength: F_ads = -G_wall psi(x) sum_a w_a s(x+e_a) e_a at walls */
+} lbpc_params;
+
+/* Library version (LBPC_VERSION). */
+int32_t lbpc_version(void);
+
+/* Validate a parameter set. Returns LBPC_OK or LBPC_EINVAL and writes a reason into msg
+ * (NUL-terminated, at most msg_len bytes) when msg is not NULL. No device work. */
+lbpc_status lbpc_check_params(const lbpc_params* p, char* msg, size_t msg_len);
+
+/* Bytes of device workspace a context with these parameters needs (0 if the parameters are
+ * invalid). The caller allocates it (any device allocation aligned to 256 bytes). */
+size_t lbpc_workspace_bytes(const lbpc_params* p);
+
+/* Critical temperature and pressure of the Peng-Robinson EOS: T_c = 0.0778 a / (0.45724 b R),
+ * p_c = 0.0778 R T_c / b (both follow from the definitions of a and b after Eq. 56). Host only. */
+lbpc_status lbpc_eos_critical(const lbpc_params* p, double* Tc, double* pc);
+
+/* Liquid-vapor coexistence of Eq. 56 at temperature T < T_c (equal pressure and equal fugacity):
+ * writes rho_v < rho_l and the saturation pressure. Host only; LBPC_EINVAL if T >= T_c. */
+lbpc_status lbpc_coexistence(const lbpc_params* p, double T, double* rho_v, double* rho_l, double* p_sat);
+
+/* Create a context on the current CUDA device. d_workspace: caller-owned device buffer of at least
+ * lbpc_workspace_bytes(p) bytes, borrowed until lbpc_destroy. stream: a cudaStream_t (NULL = the
+ * legacy default stream). The populations are undefined until lbpc_init. */
+lbpc_status lbpc_create(const lbpc_params* p, void* d_workspace, size_t bytes, void* stream, lbpc_ctx** out);
+
+/* Set the state to equilibrium populations f = M^{-1} m_eq(rho, u), g = M^{-1} m_eq(T, u), closed
+ * once by the boundary step, and reset the step counter. rho, T: [ny][nx] FP64 (required);
+ * ux, uy: [ny][nx] FP64 or NULL for zero. Synchronises the stream. */
+lbpc_status lbpc_init(lbpc_ctx* c, const double* rho, const double* T, const double* ux, const double* uy,
+                      int on_device);
+
+/* Advance n >= 0 time steps and check the device status word once at the end (synchronises the
+ * stream). Returns LBPC_ENONPHYS with step, x, y in lbpc_last_error if a node left the physical
+ * range of the EOS during these steps. */
+lbpc_status lbpc_step(lbpc_ctx* c, int64_t n);
+
+/* Enqueue n time steps on the stream and return without synchronising or checking the device
+ * status; the next lbpc_step / lbpc_fields / lbpc_sums / lbpc_check reports any error. */
+lbpc_status lbpc_step_async(lbpc_ctx* c, int64_t n);
+
+/* Advance exactly one time step with a CUDA event recorded on the context's stream before the first
+ * kernel and after each kernel of the step; synchronise and write the duration of each kernel launch
+ * in milliseconds to kernel_ms[0 .. *n_kernels) (at most max_kernels entries). lbpc_kernel_name
+ * names them. Used to time the step's kernels live inside a benchmark. */
+lbpc_status lbpc_step_timed(lbpc_ctx* c, float* kernel_ms, int32_t max_kernels, int32_t* n_kernels);
+
+/* Name of kernel k of the step as lbpc_step_timed orders them ("" if k is out of range). */
+const char* lbpc_kernel_name(const lbpc_ctx* c, int32_t k);
+
+/* Synchronise the stream and check the device status word. */
+lbpc_status lbpc_check(lbpc_ctx* c);
+
+/* Macroscopic fields of the current state: rho = sum f, u = (sum e f + F/2)/rho (F as the next step
+ * would use it), T = sum g. Any pointer may be NULL. [ny][nx] FP64. Synchronises the stream. */
+lbpc_status lbpc_fields(lbpc_ctx* c, double* rho, double* ux, double* uy, double* T, int on_device);
+
+/* Domain sums of rho (mass) and T (heat content) of the current state, accumulated in FP64 in a
+ * fixed order. Synchronises the stream. */
+lbpc_status lbpc_sums(lbpc_ctx* c, double* mass, double* heat);
+
+/* Raw populations of the current state in post-stream, post-boundary form: f, g are [9][ny][nx]
+ * FP64 (D2Q9 order e0=(0,0), e1=(1,0), e2=(0,1), e3=(-1,0), e4=(0,-1), e5=(1,1), e6=(-1,1),
+ * e7=(-1,-1), e8=(1,-1)). Either pointer may be NULL. Synchronises the stream. */
+lbpc_status lbpc_populations(lbpc_ctx* c, double* f, double* g, int on_device);
+
+/* Number of time steps taken since lbpc_init. */
+int64_t lbpc_step_count(const lbpc_ctx* c);
+
+/* Message of the last error of the context ("" if none). Valid until the next call on c. */
+const char* lbpc_last_error(const lbpc_ctx* c);
+
+/* Free the context (not the workspace, not the stream). NULL is allowed. */
+void lbpc_destroy(lbpc_ctx* c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBPC_H */

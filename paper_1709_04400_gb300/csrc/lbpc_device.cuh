@@ -1,0 +1,275 @@
+// Device-side building blocks of the coupled step: D2Q9 lattice, Peng-Robinson EOS, boundary
+// closures, moment transforms and the two MRT collisions. Every kernel of liblbpc composes these,
+// so that the split and fused kernels compute the same arithmetic.
+//
+// D2Q9 order: e0=(0,0) e1=(1,0) e2=(0,1) e3=(-1,0) e4=(0,-1) e5=(1,1) e6=(-1,1) e7=(-1,-1) e8=(1,-1);
+// weights 4/9, 1/9, 1/36 (Sec. II B). Moments (rho, e, eps, jx, qx, jy, qy, pxx, pxy): the orthogonal
+// MRT basis of Eqs. 42-43, whose thermal equilibria are Eq. 53.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbpc {
+
+enum { BC_PERIODIC = 0, BC_WALL = 1, BC_PRESSURE = 2 };
+enum { ST_RHO_LE0 = 1, ST_RHO_POLE = 2, ST_T_LE0 = 3, ST_PSI2_NEG = 4, ST_NONFINITE = 5 };
+
+__host__ __device__ constexpr int EX(int a) { return a == 1 || a == 5 || a == 8 ? 1 : (a == 3 || a == 6 || a == 7 ? -1 : 0); }
+__host__ __device__ constexpr int EY(int a) { return a == 2 || a == 5 || a == 6 ? 1 : (a == 4 || a == 7 || a == 8 ? -1 : 0); }
+
+// Everything a kernel needs, derived once on the host from lbpc_params and passed by value.
+struct DevParams {
+  int nx, ny;
+  long long N;       // nx * ny
+  int yper;          // y periodic
+  int ybc_lo, ybc_hi;
+  int tbc[4];
+  int strip_x0, strip_x1;
+  int model;         // 0 improved, 1 compromised
+  int lambda_mode;   // 0 const, 1 rho cV chi
+  int buoyancy;
+  double T_bc[4], T_strip;
+  double rho_bc_lo, rho_bc_hi;
+  double a, b, R, G, Tc, kappa;
+  double s_f[9], s_g[9];
+  double qcoef;      // 12 sigma / (1/s_e - 1/2)
+  double lambda, chi, cV, kdiff;  // kdiff = (1/s_g3 - 1/2) c_s^2
+  double gx, gy, G_wall;
+  double c3, c5;     // (1 - s3/2) s4, (1 - s5/2) s6 of Eqs. 54-55
+};
+
+template <class S> __device__ __forceinline__ double ld(const S* p) { return (double)__ldg(p); }
+
+// ------------------------------------------------------------------------------------------------
+// moment transforms: m = M x and x = M^{-1} m with M^{-1} = M^T diag(1/9,1/36,1/36,1/6,1/12,1/6,1/12,1/4,1/4)
+// ------------------------------------------------------------------------------------------------
+template <class R> __device__ __forceinline__ void to_moments(const R x[9], R m[9]) {
+  const R s14 = x[1] + x[2] + x[3] + x[4];
+  const R s58 = x[5] + x[6] + x[7] + x[8];
+  const R d13 = x[1] - x[3], d24 = x[2] - x[4];
+  const R px = x[5] - x[6] - x[7] + x[8];
+  const R py = x[5] + x[6] - x[7] - x[8];
+  m[0] = x[0] + s14 + s58;
+  m[1] = R(-4) * x[0] - s14 + R(2) * s58;
+  m[2] = R(4) * x[0] - R(2) * s14 + s58;
+  m[3] = d13 + px;
+  m[4] = R(-2) * d13 + px;
+  m[5] = d24 + py;
+  m[6] = R(-2) * d24 + py;
+  m[7] = x[1] - x[2] + x[3] - x[4];
+  m[8] = x[5] - x[6] + x[7] - x[8];
+}
+
+template <class R> __device__ __forceinline__ void from_moments(const R m[9], R x[9]) {
+  const R u0 = m[0] * R(1.0 / 9.0), u1 = m[1] * R(1.0 / 36.0), u2 = m[2] * R(1.0 / 36.0);
+  const R u3 = m[3] * R(1.0 / 6.0), u4 = m[4] * R(1.0 / 12.0), u5 = m[5] * R(1.0 / 6.0);
+  const R u6 = m[6] * R(1.0 / 12.0), u7 = m[7] * R(0.25), u8 = m[8] * R(0.25);
+  const R ax = u0 - u1 - R(2) * u2;  // common to e1..e4
+  const R dg = u0 + R(2) * u1 + u2;  // common to e5..e8
+  const R qx = u3 - R(2) * u4, qy = u5 - R(2) * u6;
+  const R sx = u3 + u4, sy = u5 + u6;
+  x[0] = u0 - R(4) * u1 + R(4) * u2;
+  x[1] = ax + qx + u7;
+  x[2] = ax + qy - u7;
+  x[3] = ax - qx + u7;
+  x[4] = ax - qy - u7;
+  x[5] = dg + sx + sy + u8;
+  x[6] = dg - sx + sy - u8;
+  x[7] = dg - sx - sy + u8;
+  x[8] = dg + sx - sy - u8;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Peng-Robinson EOS (Eq. 56) and (dp/dT)_rho
+// ------------------------------------------------------------------------------------------------
+template <class R> __device__ __forceinline__ void eos(R rho, R T, const DevParams& P, R& p, R& dpdT) {
+  const R sq = sqrt(T / R(P.Tc));                   // sqrt(T / T_c)
+  const R th1 = R(1) + R(P.kappa) * (R(1) - sq);
+  const R theta = th1 * th1;
+  const R dtheta = -R(P.kappa) * th1 / (sq * R(P.Tc));  // d theta/dT = -kappa th1 / sqrt(T T_c)
+  const R br = R(P.b) * rho;
+  const R inv1 = R(1) / (R(1) - br);
+  const R inv2 = R(1) / (R(1) + R(2) * br - br * br);
+  const R r2 = rho * rho;
+  p = rho * R(P.R) * T * inv1 - R(P.a) * theta * r2 * inv2;
+  dpdT = rho * R(P.R) * inv1 - R(P.a) * dtheta * r2 * inv2;
+}
+
+// ------------------------------------------------------------------------------------------------
+// pull-stream with the boundary closures applied at the pulling node
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ int wrapx(int x, int nx) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); }
+
+// Post-stream population a at (x, y): src holds post-collision populations (SoA [9][N]); a
+// population whose source node lies beyond a non-periodic y edge is unknown and returned as 0.
+template <class S, class R>
+__device__ __forceinline__ void pull(const S* __restrict__ src, const DevParams& P, int x, int y, R v[9]) {
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    const int sx = wrapx(x - EX(a), P.nx);
+    int sy = y - EY(a);
+    if (P.yper) {
+      sy = sy < 0 ? sy + P.ny : (sy >= P.ny ? sy - P.ny : sy);
+    } else if (sy < 0 || sy >= P.ny) {
+      v[a] = R(0);
+      continue;
+    }
+    v[a] = R(ld(src + (long long)a * P.N + (long long)sy * P.nx + sx));
+  }
+}
+
+// Zou-He closure of the unknown f on a non-periodic y edge (wall: u = 0; pressure: rho = rho_bc, u_x = 0).
+template <class R> __device__ __forceinline__ void flow_closure(R f[9], const DevParams& P, int y) {
+  if (P.yper) return;
+  const R d13 = f[1] - f[3];
+  if (y == 0) {
+    if (P.ybc_lo == BC_WALL) {
+      f[2] = f[4];
+      f[5] = f[7] - R(0.5) * d13;
+      f[6] = f[8] + R(0.5) * d13;
+    } else {
+      const R ru = R(P.rho_bc_lo) - (f[0] + f[1] + f[3] + R(2) * (f[4] + f[7] + f[8]));  // rho_bc u_y
+      f[2] = f[4] + R(2.0 / 3.0) * ru;
+      f[5] = f[7] - R(0.5) * d13 + ru * R(1.0 / 6.0);
+      f[6] = f[8] + R(0.5) * d13 + ru * R(1.0 / 6.0);
+    }
+  } else if (y == P.ny - 1) {
+    if (P.ybc_hi == BC_WALL) {
+      f[4] = f[2];
+      f[7] = f[5] + R(0.5) * d13;
+      f[8] = f[6] - R(0.5) * d13;
+    } else {
+      const R ru = (f[0] + f[1] + f[3] + R(2) * (f[2] + f[5] + f[6])) - R(P.rho_bc_hi);  // rho_bc u_y
+      f[4] = f[2] - R(2.0 / 3.0) * ru;
+      f[7] = f[5] + R(0.5) * d13 - ru * R(1.0 / 6.0);
+      f[8] = f[6] - R(0.5) * d13 - ru * R(1.0 / 6.0);
+    }
+  }
+}
+
+// Thermal equilibrium moments (Eq. 53 for the improved model, Eq. 44 for the compromised one).
+template <class R> __device__ __forceinline__ void heat_meq(R T, R vx, R vy, int model, R n[9]) {
+  n[0] = T;
+  n[1] = R(-2) * T;
+  n[2] = model == 0 ? R(2) * T : T;
+  n[3] = T * vx;
+  n[4] = -T * vx;
+  n[5] = T * vy;
+  n[6] = -T * vy;
+  n[7] = R(0);
+  n[8] = R(0);
+}
+
+// Thermal boundary step: bounce-back of the unknown g on non-periodic y edges, then Dirichlet
+// nodes g := M^{-1} m_eq(T_bc, 0) (x edges, then y edges, then the heated strip).
+template <class R> __device__ __forceinline__ void heat_closure(R g[9], const DevParams& P, int x, int y) {
+  if (!P.yper) {
+    if (y == 0) { g[2] = g[4]; g[5] = g[7]; g[6] = g[8]; }
+    if (y == P.ny - 1) { g[4] = g[2]; g[7] = g[5]; g[8] = g[6]; }
+  }
+  bool set = false;
+  double Tb = 0.0;
+  if (x == 0 && P.tbc[0]) { set = true; Tb = P.T_bc[0]; }
+  if (x == P.nx - 1 && P.tbc[1]) { set = true; Tb = P.T_bc[1]; }
+  if (y == 0 && P.tbc[2]) { set = true; Tb = (x >= P.strip_x0 && x < P.strip_x1) ? P.T_strip : P.T_bc[2]; }
+  if (y == P.ny - 1 && P.tbc[3]) { set = true; Tb = P.T_bc[3]; }
+  if (set) {
+    R n[9];
+    heat_meq(R(Tb), R(0), R(0), P.model, n);
+    from_moments(n, g);
+  }
+}
+
+// Post-stream, post-boundary f and g at (x, y).
+template <class S, class R>
+__device__ __forceinline__ void pull_closed(const S* __restrict__ fsrc, const S* __restrict__ gsrc, const DevParams& P,
+                                            int x, int y, R f[9], R g[9]) {
+  pull<S, R>(fsrc, P, x, y, f);
+  pull<S, R>(gsrc, P, x, y, g);
+  flow_closure(f, P, y);
+  heat_closure(g, P, x, y);
+}
+
+// ------------------------------------------------------------------------------------------------
+// collisions
+// ------------------------------------------------------------------------------------------------
+// Flow MRT collision with forcing (reading of the improved pseudopotential model, Refs. [13,29]):
+// m* = m - Lambda (m - m_eq) + (I - Lambda/2) S_F, S_F with the sigma term Q in the energy moments.
+template <class R>
+__device__ __forceinline__ void collide_flow(R f[9], R rho, R vx, R vy, R Fx, R Fy, R Q, const DevParams& P) {
+  R m[9];
+  to_moments(f, m);
+  const R v2 = vx * vx + vy * vy;
+  const R vF = vx * Fx + vy * Fy;
+  R meq[9], SF[9];
+  meq[0] = rho;                       SF[0] = R(0);
+  meq[1] = rho * (R(-2) + R(3) * v2); SF[1] = R(6) * vF + Q;
+  meq[2] = rho * (R(1) - R(3) * v2);  SF[2] = R(-6) * vF - Q;
+  meq[3] = rho * vx;                  SF[3] = Fx;
+  meq[4] = -rho * vx;                 SF[4] = -Fx;
+  meq[5] = rho * vy;                  SF[5] = Fy;
+  meq[6] = -rho * vy;                 SF[6] = -Fy;
+  meq[7] = rho * (vx * vx - vy * vy); SF[7] = R(2) * (vx * Fx - vy * Fy);
+  meq[8] = rho * vx * vy;             SF[8] = vx * Fy + vy * Fx;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) m[k] = m[k] - R(P.s_f[k]) * (m[k] - meq[k]) + (R(1) - R(0.5) * R(P.s_f[k])) * SF[k];
+  from_moments(m, f);
+}
+
+// Thermal MRT collision of the improved model: Eq. 45 with m_eq of Eq. 53 and S = (S0, 0, ..., 0)
+// (Eq. 46), then m3* += (1 - s3/2) s4 (m4 - m4_eq) and m5* += (1 - s5/2) s6 (m6 - m6_eq) (Eqs. 54-55).
+template <class R> __device__ __forceinline__ void collide_heat(R g[9], R T, R vx, R vy, R S0, const DevParams& P) {
+  R n[9], neq[9];
+  to_moments(g, n);
+  heat_meq(T, vx, vy, P.model, neq);
+  R ns[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) ns[k] = n[k] - R(P.s_g[k]) * (n[k] - neq[k]);
+  ns[0] += S0;
+  if (P.model == 0) {
+    ns[3] += R(P.c3) * (n[4] - neq[4]);
+    ns[5] += R(P.c5) * (n[6] - neq[6]);
+  }
+  from_moments(ns, g);
+}
+
+// ------------------------------------------------------------------------------------------------
+// block reduction (fixed order: warp shuffle tree, then warp 0 over the warp sums)
+// ------------------------------------------------------------------------------------------------
+template <int BLOCK> __device__ __forceinline__ double block_sum(double v, double* smem) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) smem[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (w == 0) {
+    s = lane < BLOCK / 32 ? smem[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  __syncthreads();
+  return s;  // valid in thread 0
+}
+
+// Record the first non-physical node (step, x, y, code); later reports are dropped.
+__device__ __forceinline__ void report(long long* status, long long step, int x, int y, int code) {
+  if (atomicCAS((unsigned long long*)status, 0ull, 1ull) == 0ull) {
+    status[1] = step;
+    status[2] = x;
+    status[3] = y;
+    status[4] = code;
+  }
+}
+
+template <class R> __device__ __forceinline__ int classify(R rho, R T, R psi2, const DevParams& P) {
+  if (!isfinite(rho) || !isfinite(T) || !isfinite(psi2)) return ST_NONFINITE;
+  if (!(rho > R(0))) return ST_RHO_LE0;
+  if (!(R(P.b) * rho < R(1))) return ST_RHO_POLE;
+  if (!(T > R(0))) return ST_T_LE0;
+  if (!(psi2 >= R(0))) return ST_PSI2_NEG;
+  return 0;
+}
+
+}  // namespace lbpc

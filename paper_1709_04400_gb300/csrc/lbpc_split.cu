@@ -1,0 +1,382 @@
+// Split form of the coupled step: three node-parallel kernels per time step.
+//
+//   k_macro    pull-stream + boundary closures; rho, j, T (moments), p_EOS -> psi and (dp/dT)_rho
+//              (Eq. 56); optional per-block partial sums of rho for the buoyancy reference rho_ave.
+//   k_force    psi stencil -> F = F_int + F_ads + F_b, v = (j + F/2)/rho, sigma term Q.
+//   k_collide  pull again (same closures); isotropic grad T, lap T, grad rho, div v; source phi of
+//              Eq. 28 and S0 of Eq. 46; flow MRT collide with forcing; thermal MRT collide with the
+//              corrections of Eqs. 54-55; store post-collision f*, g* (pull scheme, A/B buffers).
+//
+// Each kernel reads its node's stencil straight from global memory (L1/L2 serve the reuse). With
+// FP64 arithmetic the step is bound by the FP64 pipe, not by HBM, and this split computes every
+// EOS evaluation, force and velocity exactly once per node and step.
+#include "lbpc_device.cuh"
+#include "lbpc_internal.h"
+
+namespace lbpc {
+
+constexpr int BLOCK = 256;
+
+// Planes of the split path's scratch (type R, N nodes each).
+enum { P_RHO = 0, P_T, P_PSI, P_JX, P_JY, P_DPDT, P_VX, P_VY, P_FX, P_FY, P_Q, NPLANES };
+
+template <class R> struct Planes {
+  R* p[NPLANES];
+};
+
+__device__ __forceinline__ long long node_index(const DevParams& P, int x, int y) { return (long long)y * P.nx + x; }
+
+// Neighbour row for a stencil: wraps when y is periodic, else clamps to the edge row (ghost rows
+// copy the edge row). out_lo/out_hi report a ghost beyond the lower / upper edge.
+__device__ __forceinline__ int nb_row(const DevParams& P, int y, int dy, bool& ghost_lo, bool& ghost_hi) {
+  int yy = y + dy;
+  ghost_lo = ghost_hi = false;
+  if (P.yper) return yy < 0 ? yy + P.ny : (yy >= P.ny ? yy - P.ny : yy);
+  if (yy < 0) { ghost_lo = true; return 0; }
+  if (yy >= P.ny) { ghost_hi = true; return P.ny - 1; }
+  return yy;
+}
+
+// Gather the 3x3 neighbourhood c[dy+1][dx+1] of a plane with the copy-ghost rule.
+template <class R> __device__ __forceinline__ void gather9(const R* __restrict__ X, const DevParams& P, int x, int y, R c[3][3]) {
+  const int xm = wrapx(x - 1, P.nx), xp = wrapx(x + 1, P.nx);
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy) {
+    bool lo, hi;
+    const long long row = (long long)nb_row(P, y, dy, lo, hi) * P.nx;
+    c[dy + 1][0] = __ldg(X + row + xm);
+    c[dy + 1][1] = __ldg(X + row + x);
+    c[dy + 1][2] = __ldg(X + row + xp);
+  }
+}
+
+// Isotropic differences (reading of the paper's cited stencils): d_i X = 3 sum_a w_a X(x+e_a) e_ai,
+// lap X = 6 sum_a w_a (X(x+e_a) - X(x)). c[1][1] is the centre, c[2][*] the row above.
+template <class R> __device__ __forceinline__ R d_x(const R c[3][3]) {
+  return (c[1][2] - c[1][0]) * R(1.0 / 3.0) + (c[2][2] - c[2][0] - c[0][0] + c[0][2]) * R(1.0 / 12.0);
+}
+template <class R> __device__ __forceinline__ R d_y(const R c[3][3]) {
+  return (c[2][1] - c[0][1]) * R(1.0 / 3.0) + (c[2][2] + c[2][0] - c[0][0] - c[0][2]) * R(1.0 / 12.0);
+}
+template <class R> __device__ __forceinline__ R lap(const R c[3][3]) {
+  const R ctr = c[1][1];
+  return (c[1][2] + c[1][0] + c[2][1] + c[0][1] - R(4) * ctr) * R(2.0 / 3.0) +
+         (c[2][2] + c[2][0] + c[0][0] + c[0][2] - R(4) * ctr) * R(1.0 / 6.0);
+}
+
+template <class S, class R>
+__global__ void __launch_bounds__(BLOCK) k_macro(const S* __restrict__ fsrc, const S* __restrict__ gsrc, Planes<R> pl,
+                                                 DevParams P, long long step, int do_partials,
+                                                 double* __restrict__ partials, long long* __restrict__ status) {
+  __shared__ double red[BLOCK / 32];
+  const long long i = (long long)blockIdx.x * BLOCK + threadIdx.x;
+  double rho_d = 0.0;
+  if (i < P.N) {
+    const int y = (int)(i / P.nx), x = (int)(i - (long long)y * P.nx);
+    R f[9], g[9];
+    pull_closed<S, R>(fsrc, gsrc, P, x, y, f, g);
+    const R rho = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+    const R jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
+    const R jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
+    const R T = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
+    R p, dpdT;
+    eos(rho, T, P, p, dpdT);
+    const R psi2 = R(2) * (p - rho * R(1.0 / 3.0)) / R(P.G);
+    const int bad = classify(rho, T, psi2, P);
+    if (bad) report(status, step, x, y, bad);
+    pl.p[P_RHO][i] = rho;
+    pl.p[P_T][i] = T;
+    pl.p[P_PSI][i] = sqrt(fmax(psi2, R(0)));
+    pl.p[P_JX][i] = jx;
+    pl.p[P_JY][i] = jy;
+    pl.p[P_DPDT][i] = dpdT;
+    rho_d = (double)rho;
+  }
+  if (do_partials) {
+    const double s = block_sum<BLOCK>(rho_d, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(BLOCK) k_force(Planes<R> pl, DevParams P, const double* __restrict__ rho_ave) {
+  const long long i = (long long)blockIdx.x * BLOCK + threadIdx.x;
+  if (i >= P.N) return;
+  const int y = (int)(i / P.nx), x = (int)(i - (long long)y * P.nx);
+  const R* __restrict__ psi = pl.p[P_PSI];
+  R c[3][3];
+  gather9(psi, P, x, y, c);
+  // F_int = -G psi(x) sum_a w(|e_a|^2) psi(x+e_a) e_a, w(1) = 1/3, w(2) = 1/12; a wall ghost has psi = 0.
+  if (!P.yper) {
+    if (y == 0 && P.ybc_lo == BC_WALL) c[0][0] = c[0][1] = c[0][2] = R(0);
+    if (y == P.ny - 1 && P.ybc_hi == BC_WALL) c[2][0] = c[2][1] = c[2][2] = R(0);
+  }
+  const R pc = psi[i];
+  const R sx = (c[1][2] - c[1][0]) * R(1.0 / 3.0) + (c[2][2] - c[2][0] - c[0][0] + c[0][2]) * R(1.0 / 12.0);
+  const R sy = (c[2][1] - c[0][1]) * R(1.0 / 3.0) + (c[2][2] + c[2][0] - c[0][0] - c[0][2]) * R(1.0 / 12.0);
+  const R Fix = -R(P.G) * pc * sx, Fiy = -R(P.G) * pc * sy;
+  R Fx = Fix, Fy = Fiy;
+  // F_ads = -G_w psi(x) sum_a w_a s(x+e_a) e_a: the solid ghost row gives sum = (0, -1/2) below, (0, 1/2) above.
+  if (!P.yper) {
+    if (y == 0 && P.ybc_lo == BC_WALL) Fy += R(0.5) * R(P.G_wall) * pc;
+    if (y == P.ny - 1 && P.ybc_hi == BC_WALL) Fy -= R(0.5) * R(P.G_wall) * pc;
+  }
+  const R rho = pl.p[P_RHO][i];
+  if (P.buoyancy) {  // F_b = (rho - rho_ave) g (Sec. IV B)
+    const R dr = rho - R(*rho_ave);
+    Fx += dr * R(P.gx);
+    Fy += dr * R(P.gy);
+  }
+  const R inv_rho = R(1) / rho;
+  pl.p[P_VX][i] = (pl.p[P_JX][i] + R(0.5) * Fx) * inv_rho;
+  pl.p[P_VY][i] = (pl.p[P_JY][i] + R(0.5) * Fy) * inv_rho;
+  pl.p[P_FX][i] = Fx;
+  pl.p[P_FY][i] = Fy;
+  pl.p[P_Q][i] = R(P.qcoef) * (Fix * Fix + Fiy * Fiy) / (pc * pc);
+}
+
+template <class S, class R>
+__global__ void __launch_bounds__(BLOCK) k_collide(const S* __restrict__ fsrc, const S* __restrict__ gsrc,
+                                                   S* __restrict__ fdst, S* __restrict__ gdst, Planes<R> pl,
+                                                   R* __restrict__ phi_prev, DevParams P, int first) {
+  const long long i = (long long)blockIdx.x * BLOCK + threadIdx.x;
+  if (i >= P.N) return;
+  const int y = (int)(i / P.nx), x = (int)(i - (long long)y * P.nx);
+  R f[9], g[9];
+  pull_closed<S, R>(fsrc, gsrc, P, x, y, f, g);
+  const R rho = pl.p[P_RHO][i];
+  const R T = pl.p[P_T][i];
+  const R vx = pl.p[P_VX][i], vy = pl.p[P_VY][i];
+  // gradients feeding the source (isotropic differences)
+  R c[3][3];
+  gather9(pl.p[P_T], P, x, y, c);
+  const R gTx = d_x(c), gTy = d_y(c), lapT = lap(c);
+  gather9(pl.p[P_VX], P, x, y, c);
+  R divv = d_x(c);
+  gather9(pl.p[P_VY], P, x, y, c);
+  divv += d_y(c);
+  const R rcv = rho * R(P.cV);
+  const R inv_rcv = R(1) / rcv;
+  R div_lam_gradT;
+  if (P.lambda_mode == 0) {
+    div_lam_gradT = R(P.lambda) * lapT;
+  } else {  // lambda = rho c_V chi: lambda lap T + c_V chi grad rho . grad T
+    gather9(pl.p[P_RHO], P, x, y, c);
+    div_lam_gradT = rcv * R(P.chi) * lapT + R(P.cV) * R(P.chi) * (d_x(c) * gTx + d_y(c) * gTy);
+  }
+  // phi: the underlined terms of Eq. 28 with k = (1/s_3 - 1/2) c_s^2
+  const R phi = div_lam_gradT * inv_rcv - R(P.kdiff) * lapT + T * (R(1) - pl.p[P_DPDT][i] * inv_rcv) * divv;
+  R S0 = phi;
+  if (P.model == 0) {  // S0 = phi + 0.5 dt d_t phi, d_t phi ~ [phi(t) - phi(t - dt)]/dt (Eq. 46)
+    const R pp = first ? phi : phi_prev[i];
+    S0 = phi + R(0.5) * (phi - pp);
+  }
+  phi_prev[i] = phi;
+  collide_flow(f, rho, vx, vy, pl.p[P_FX][i], pl.p[P_FY][i], pl.p[P_Q][i], P);
+  collide_heat(g, T, vx, vy, S0, P);
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    fdst[(long long)a * P.N + i] = (S)f[a];
+    gdst[(long long)a * P.N + i] = (S)g[a];
+  }
+}
+
+// Fixed-order sum of the block partials: each thread accumulates a strided subset in order, then one
+// block reduction. out[k] = sum(partials[k * stride + 0 .. n)) * scale.
+__global__ void __launch_bounds__(BLOCK) k_finish(const double* __restrict__ partials, int n, int stride, int count,
+                                                  double scale, double* __restrict__ out) {
+  __shared__ double red[BLOCK / 32];
+  for (int k = 0; k < count; ++k) {
+    double s = 0.0;
+    for (int j = threadIdx.x; j < n; j += BLOCK) s += partials[(long long)k * stride + j];
+    s = block_sum<BLOCK>(s, red);
+    if (threadIdx.x == 0) out[k] = s * scale;
+  }
+}
+
+// Equilibrium start: writes post-collision-layout buffers whose pull gives f = M^{-1} m_eq(rho, u),
+// g = M^{-1} m_eq(T, u) at every node (the slot that node x pulls for direction a sits at x - e_a).
+template <class S>
+__global__ void __launch_bounds__(BLOCK) k_init(const double* __restrict__ rho_in, const double* __restrict__ T_in,
+                                                const double* __restrict__ ux_in, const double* __restrict__ uy_in,
+                                                S* __restrict__ f, S* __restrict__ g, DevParams P) {
+  const long long i = (long long)blockIdx.x * BLOCK + threadIdx.x;
+  if (i >= P.N) return;
+  const int y = (int)(i / P.nx), x = (int)(i - (long long)y * P.nx);
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    // node whose pull reads slot (x, y) in direction a
+    const int tx = wrapx(x + EX(a), P.nx);
+    int ty = y + EY(a);
+    if (ty < 0 || ty >= P.ny) {
+      if (!P.yper) {  // no node pulls this slot; keep it finite
+        f[(long long)a * P.N + i] = (S)0.0;
+        g[(long long)a * P.N + i] = (S)0.0;
+        continue;
+      }
+      ty = ty < 0 ? ty + P.ny : ty - P.ny;
+    }
+    const long long t = (long long)ty * P.nx + tx;
+    const double rho = rho_in[t], T = T_in[t];
+    const double vx = ux_in ? ux_in[t] : 0.0, vy = uy_in ? uy_in[t] : 0.0;
+    const double v2 = vx * vx + vy * vy;
+    double m[9], fe[9], ge[9];
+    m[0] = rho; m[1] = rho * (-2.0 + 3.0 * v2); m[2] = rho * (1.0 - 3.0 * v2);
+    m[3] = rho * vx; m[4] = -rho * vx; m[5] = rho * vy; m[6] = -rho * vy;
+    m[7] = rho * (vx * vx - vy * vy); m[8] = rho * vx * vy;
+    from_moments(m, fe);
+    heat_meq(T, vx, vy, P.model, m);
+    from_moments(m, ge);
+    f[(long long)a * P.N + i] = (S)fe[a];
+    g[(long long)a * P.N + i] = (S)ge[a];
+  }
+}
+
+// Sums of rho and T over the current (post-boundary) state into per-block partials.
+template <class S>
+__global__ void __launch_bounds__(BLOCK) k_sums(const S* __restrict__ fsrc, const S* __restrict__ gsrc, DevParams P,
+                                                double* __restrict__ partials, int stride) {
+  __shared__ double red[BLOCK / 32];
+  const long long i = (long long)blockIdx.x * BLOCK + threadIdx.x;
+  double r = 0.0, t = 0.0;
+  if (i < P.N) {
+    const int y = (int)(i / P.nx), x = (int)(i - (long long)y * P.nx);
+    double f[9], g[9];
+    pull_closed<S, double>(fsrc, gsrc, P, x, y, f, g);
+    r = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+    t = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
+  }
+  const double sr = block_sum<BLOCK>(r, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = sr;
+  const double st = block_sum<BLOCK>(t, red);
+  if (threadIdx.x == 0) partials[stride + blockIdx.x] = st;
+}
+
+// Post-boundary populations of the current state as FP64 [9][N] (which = 0: f, 1: g).
+template <class S>
+__global__ void __launch_bounds__(BLOCK) k_export_pops(const S* __restrict__ fsrc, const S* __restrict__ gsrc,
+                                                       DevParams P, int which, double* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * BLOCK + threadIdx.x;
+  if (i >= P.N) return;
+  const int y = (int)(i / P.nx), x = (int)(i - (long long)y * P.nx);
+  double f[9], g[9];
+  pull_closed<S, double>(fsrc, gsrc, P, x, y, f, g);
+#pragma unroll
+  for (int a = 0; a < 9; ++a) out[(long long)a * P.N + i] = which ? g[a] : f[a];
+}
+
+// Copy planes rho, vx, vy, T to FP64 outputs (any may be null).
+template <class R>
+__global__ void __launch_bounds__(BLOCK) k_export_fields(Planes<R> pl, DevParams P, double* rho, double* ux, double* uy,
+                                                         double* T) {
+  const long long i = (long long)blockIdx.x * BLOCK + threadIdx.x;
+  if (i >= P.N) return;
+  if (rho) rho[i] = (double)pl.p[P_RHO][i];
+  if (ux) ux[i] = (double)pl.p[P_VX][i];
+  if (uy) uy[i] = (double)pl.p[P_VY][i];
+  if (T) T[i] = (double)pl.p[P_T][i];
+}
+
+// ------------------------------------------------------------------------------------------------
+// host launchers
+// ------------------------------------------------------------------------------------------------
+static inline unsigned blocks_for(long long N) { return (unsigned)((N + BLOCK - 1) / BLOCK); }
+
+template <class S, class R> static Planes<R> planes_of(const SplitBuffers& b) {
+  Planes<R> pl;
+  for (int k = 0; k < NPLANES; ++k) pl.p[k] = (R*)b.planes[k];
+  return pl;
+}
+
+template <class S, class R>
+static cudaError_t step_impl(const SplitBuffers& b, const DevParams& P, int cur, long long step, cudaStream_t st,
+                             cudaEvent_t* ev) {
+  const unsigned nb = blocks_for(P.N);
+  const S* fs = (const S*)b.f[cur];
+  const S* gs = (const S*)b.g[cur];
+  Planes<R> pl = planes_of<S, R>(b);
+  if (ev) cudaEventRecord(ev[0], st);
+  k_macro<S, R><<<nb, BLOCK, 0, st>>>(fs, gs, pl, P, step, P.buoyancy, b.partials, b.status);
+  if (ev) cudaEventRecord(ev[1], st);
+  k_force<R><<<nb, BLOCK, 0, st>>>(pl, P, b.scalars);
+  if (ev) cudaEventRecord(ev[2], st);
+  k_collide<S, R><<<nb, BLOCK, 0, st>>>(fs, gs, (S*)b.f[cur ^ 1], (S*)b.g[cur ^ 1], pl, (R*)b.phi_prev, P, step == 0);
+  if (ev) cudaEventRecord(ev[3], st);
+  if (P.buoyancy) {
+    k_finish<<<1, BLOCK, 0, st>>>(b.partials, (int)nb, 0, 1, 1.0 / (double)P.N, b.scalars);
+    if (ev) cudaEventRecord(ev[4], st);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t split_step(const SplitBuffers& b, const DevParams& P, int prec, int cur, long long step, cudaStream_t st,
+                       cudaEvent_t* ev) {
+  return prec == 0 ? step_impl<double, double>(b, P, cur, step, st, ev) : step_impl<float, float>(b, P, cur, step, st, ev);
+}
+
+int split_kernel_count(const DevParams& P) { return P.buoyancy ? 4 : 3; }
+
+const char* split_kernel_name(int k) {
+  static const char* names[] = {"k_macro", "k_force", "k_collide", "k_finish"};
+  return (k >= 0 && k < 4) ? names[k] : "";
+}
+
+template <class S>
+static cudaError_t init_impl(const SplitBuffers& b, const DevParams& P, const double* rho, const double* T,
+                             const double* ux, const double* uy, cudaStream_t st) {
+  const unsigned nb = blocks_for(P.N);
+  k_init<S><<<nb, BLOCK, 0, st>>>(rho, T, ux, uy, (S*)b.f[0], (S*)b.g[0], P);
+  // rho_ave of the initial (post-boundary) state
+  k_sums<S><<<nb, BLOCK, 0, st>>>((const S*)b.f[0], (const S*)b.g[0], P, b.partials, (int)nb);
+  k_finish<<<1, BLOCK, 0, st>>>(b.partials, (int)nb, (int)nb, 1, 1.0 / (double)P.N, b.scalars);
+  return cudaGetLastError();
+}
+
+cudaError_t split_init(const SplitBuffers& b, const DevParams& P, int prec, const double* rho, const double* T,
+                       const double* ux, const double* uy, cudaStream_t st) {
+  return prec == 0 ? init_impl<double>(b, P, rho, T, ux, uy, st) : init_impl<float>(b, P, rho, T, ux, uy, st);
+}
+
+template <class S>
+static cudaError_t sums_impl(const SplitBuffers& b, const DevParams& P, int cur, cudaStream_t st) {
+  const unsigned nb = blocks_for(P.N);
+  k_sums<S><<<nb, BLOCK, 0, st>>>((const S*)b.f[cur], (const S*)b.g[cur], P, b.partials, (int)nb);
+  k_finish<<<1, BLOCK, 0, st>>>(b.partials, (int)nb, (int)nb, 2, 1.0, b.scalars + 1);
+  return cudaGetLastError();
+}
+
+cudaError_t split_sums(const SplitBuffers& b, const DevParams& P, int prec, int cur, cudaStream_t st) {
+  return prec == 0 ? sums_impl<double>(b, P, cur, st) : sums_impl<float>(b, P, cur, st);
+}
+
+template <class S, class R>
+static cudaError_t fields_impl(const SplitBuffers& b, const DevParams& P, int cur, long long step, double* rho,
+                               double* ux, double* uy, double* T, cudaStream_t st) {
+  const unsigned nb = blocks_for(P.N);
+  Planes<R> pl = planes_of<S, R>(b);
+  k_macro<S, R><<<nb, BLOCK, 0, st>>>((const S*)b.f[cur], (const S*)b.g[cur], pl, P, step, 0, b.partials, b.status);
+  k_force<R><<<nb, BLOCK, 0, st>>>(pl, P, b.scalars);
+  k_export_fields<R><<<nb, BLOCK, 0, st>>>(pl, P, rho, ux, uy, T);
+  return cudaGetLastError();
+}
+
+cudaError_t split_fields(const SplitBuffers& b, const DevParams& P, int prec, int cur, long long step, double* rho,
+                         double* ux, double* uy, double* T, cudaStream_t st) {
+  return prec == 0 ? fields_impl<double, double>(b, P, cur, step, rho, ux, uy, T, st)
+                   : fields_impl<float, float>(b, P, cur, step, rho, ux, uy, T, st);
+}
+
+cudaError_t split_export_pops(const SplitBuffers& b, const DevParams& P, int prec, int cur, int which, double* out,
+                              cudaStream_t st) {
+  const unsigned nb = blocks_for(P.N);
+  if (prec == 0)
+    k_export_pops<double><<<nb, BLOCK, 0, st>>>((const double*)b.f[cur], (const double*)b.g[cur], P, which, out);
+  else
+    k_export_pops<float><<<nb, BLOCK, 0, st>>>((const float*)b.f[cur], (const float*)b.g[cur], P, which, out);
+  return cudaGetLastError();
+}
+
+int split_nplanes() { return NPLANES; }
+int split_block() { return BLOCK; }
+
+}  // namespace lbpc

@@ -1,0 +1,319 @@
+"""Python binding of liblbpc (ctypes): argument marshalling only.
+
+Every step of the computation runs in the CUDA kernels of liblbpc.so; this module fills the
+``lbpc_params`` struct declared in ``include/lbpc.h``, allocates the caller-owned device workspace
+with PyTorch, passes PyTorch's current CUDA stream, and moves FP64 fields in and out. There is no
+CPU fallback: if the library is not built, or no CUDA device is present, the calls raise.
+"""
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbpc.so")
+
+LBPC_OK, LBPC_EINVAL, LBPC_ENOMEM, LBPC_ECUDA, LBPC_ENONPHYS, LBPC_ETIMEOUT, LBPC_ESTATE = range(7)
+STATUS_NAMES = {0: "LBPC_OK", 1: "LBPC_EINVAL", 2: "LBPC_ENOMEM", 3: "LBPC_ECUDA", 4: "LBPC_ENONPHYS",
+                5: "LBPC_ETIMEOUT", 6: "LBPC_ESTATE"}
+FP64, FP32 = 0, 1
+PERIODIC, WALL, PRESSURE = 0, 1, 2
+T_NONE, T_DIRICHLET = 0, 1
+LAMBDA_CONST, LAMBDA_RHO_CV_CHI = 0, 1
+IMPROVED, COMPROMISED = 0, 1
+
+EXPORTED = ["lbpc_version", "lbpc_check_params", "lbpc_workspace_bytes", "lbpc_eos_critical", "lbpc_coexistence",
+            "lbpc_create", "lbpc_init", "lbpc_step", "lbpc_step_async", "lbpc_check", "lbpc_fields", "lbpc_sums",
+            "lbpc_populations", "lbpc_step_count", "lbpc_last_error", "lbpc_destroy", "lbpc_step_timed",
+            "lbpc_kernel_name"]
+
+
+class LbpcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class CParams(ctypes.Structure):
+    """Mirror of lbpc_params (include/lbpc.h); field order and types must match."""
+
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("prec", ctypes.c_int32), ("model", ctypes.c_int32),
+        ("lambda_mode", ctypes.c_int32), ("buoyancy", ctypes.c_int32),
+        ("flow_bc", ctypes.c_int32 * 4), ("t_bc", ctypes.c_int32 * 4),
+        ("strip_x0", ctypes.c_int32), ("strip_x1", ctypes.c_int32),
+        ("a", ctypes.c_double), ("b", ctypes.c_double), ("R", ctypes.c_double), ("omega", ctypes.c_double),
+        ("G", ctypes.c_double), ("s_f", ctypes.c_double * 9), ("s_g", ctypes.c_double * 9),
+        ("sigma", ctypes.c_double), ("lambda_", ctypes.c_double), ("chi", ctypes.c_double), ("cV", ctypes.c_double),
+        ("gx", ctypes.c_double), ("gy", ctypes.c_double), ("rho_bc", ctypes.c_double * 4),
+        ("T_bc", ctypes.c_double * 4), ("T_strip", ctypes.c_double), ("G_wall", ctypes.c_double),
+    ]
+
+
+_lib_handle = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load liblbpc.so and declare its signatures. Raises if the library is missing."""
+    global _lib_handle
+    if _lib_handle is not None:
+        return _lib_handle
+    if not os.path.exists(path):
+        raise RuntimeError(f"liblbpc.so is not built ({path}); run paper_1709_04400_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER(CParams)
+    dp = ctypes.POINTER(ctypes.c_double)
+    vp = ctypes.c_void_p
+    sig = {
+        "lbpc_version": (ctypes.c_int32, []),
+        "lbpc_check_params": (ctypes.c_int, [P, ctypes.c_char_p, ctypes.c_size_t]),
+        "lbpc_workspace_bytes": (ctypes.c_size_t, [P]),
+        "lbpc_eos_critical": (ctypes.c_int, [P, dp, dp]),
+        "lbpc_coexistence": (ctypes.c_int, [P, ctypes.c_double, dp, dp, dp]),
+        "lbpc_create": (ctypes.c_int, [P, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]),
+        "lbpc_init": (ctypes.c_int, [vp, vp, vp, vp, vp, ctypes.c_int]),
+        "lbpc_step": (ctypes.c_int, [vp, ctypes.c_int64]),
+        "lbpc_step_async": (ctypes.c_int, [vp, ctypes.c_int64]),
+        "lbpc_check": (ctypes.c_int, [vp]),
+        "lbpc_fields": (ctypes.c_int, [vp, vp, vp, vp, vp, ctypes.c_int]),
+        "lbpc_sums": (ctypes.c_int, [vp, dp, dp]),
+        "lbpc_populations": (ctypes.c_int, [vp, vp, vp, ctypes.c_int]),
+        "lbpc_step_count": (ctypes.c_int64, [vp]),
+        "lbpc_last_error": (ctypes.c_char_p, [vp]),
+        "lbpc_destroy": (None, [vp]),
+        "lbpc_step_timed": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
+                                           ctypes.POINTER(ctypes.c_int32)]),
+        "lbpc_kernel_name": (ctypes.c_char_p, [vp, ctypes.c_int32]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib_handle = lib
+    return lib
+
+
+EDGE = {"x-": 0, "x+": 1, "y-": 2, "y+": 3}
+
+
+@dataclass
+class Params:
+    """Physical and numerical parameters of a run (lattice units). Defaults are the paper's working
+    point: Peng-Robinson a = 3/49, b = 2/21, R = 1, omega = 0.344 (after Eq. 56), nu = 0.1 and
+    c_V = 5 (Sec. IV A), s_3 = s_5 = 1 (Sec. IV A)."""
+
+    nx: int
+    ny: int
+    prec: int = FP64
+    model: int = IMPROVED
+    a: float = 3.0 / 49.0
+    b: float = 2.0 / 21.0
+    R: float = 1.0
+    omega: float = 0.344
+    G: float = -1.0
+    s_f: Sequence[float] = (1.0, 0.8, 0.8, 1.0, 1.1, 1.0, 1.1, 1.25, 1.25)
+    s_g: Sequence[float] = (1.0,) * 9
+    sigma: float = 0.1
+    lambda_mode: int = LAMBDA_CONST
+    lam: float = 2.0 / 3.0
+    chi: float = 0.06
+    cV: float = 5.0
+    gx: float = 0.0
+    gy: float = 0.0
+    buoyancy: bool = False
+    flow_bc: Sequence[int] = (PERIODIC,) * 4
+    rho_bc: Sequence[float] = (0.0,) * 4
+    t_bc: Sequence[int] = (T_NONE,) * 4
+    T_bc: Sequence[float] = (0.0,) * 4
+    strip: Optional[Tuple[int, int, float]] = None
+    G_wall: float = 0.0
+
+    @staticmethod
+    def s_nu(nu):
+        """Shear rate of the flow MRT: nu = c_s^2 (1/s_nu - 1/2)."""
+        return 1.0 / (3.0 * nu + 0.5)
+
+    def to_c(self) -> CParams:
+        c = CParams()
+        c.nx, c.ny, c.prec, c.model = self.nx, self.ny, self.prec, self.model
+        c.lambda_mode, c.buoyancy = self.lambda_mode, int(bool(self.buoyancy))
+        c.flow_bc[:] = list(self.flow_bc)
+        c.t_bc[:] = list(self.t_bc)
+        if self.strip is not None:
+            c.strip_x0, c.strip_x1, c.T_strip = int(self.strip[0]), int(self.strip[1]), float(self.strip[2])
+        c.a, c.b, c.R, c.omega, c.G = self.a, self.b, self.R, self.omega, self.G
+        c.s_f[:] = [float(v) for v in self.s_f]
+        c.s_g[:] = [float(v) for v in self.s_g]
+        c.sigma, c.lambda_, c.chi, c.cV = self.sigma, self.lam, self.chi, self.cV
+        c.gx, c.gy, c.G_wall = self.gx, self.gy, self.G_wall
+        c.rho_bc[:] = [float(v) for v in self.rho_bc]
+        c.T_bc[:] = [float(v) for v in self.T_bc]
+        return c
+
+
+def check_params(p: Params):
+    lib = load_library()
+    buf = ctypes.create_string_buffer(256)
+    c = p.to_c()
+    s = lib.lbpc_check_params(ctypes.byref(c), buf, 256)
+    return s, buf.value.decode()
+
+
+def workspace_bytes(p: Params) -> int:
+    c = p.to_c()
+    return int(load_library().lbpc_workspace_bytes(ctypes.byref(c)))
+
+
+def eos_critical(p: Params):
+    c = p.to_c()
+    Tc, pc = ctypes.c_double(), ctypes.c_double()
+    s = load_library().lbpc_eos_critical(ctypes.byref(c), ctypes.byref(Tc), ctypes.byref(pc))
+    if s != LBPC_OK:
+        raise LbpcError(s, "lbpc_eos_critical")
+    return Tc.value, pc.value
+
+
+def coexistence(p: Params, T: float):
+    c = p.to_c()
+    rv, rl, ps = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    s = load_library().lbpc_coexistence(ctypes.byref(c), float(T), ctypes.byref(rv), ctypes.byref(rl), ctypes.byref(ps))
+    if s != LBPC_OK:
+        raise LbpcError(s, f"lbpc_coexistence(T={T})")
+    return rv.value, rl.value, ps.value
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if isinstance(a, np.ndarray) else ctypes.c_void_p(a.data_ptr())
+
+
+class Simulation:
+    """One simulation on one CUDA device: a context of liblbpc over a PyTorch-owned workspace."""
+
+    def __init__(self, params: Params, device=None, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("liblbpc needs a CUDA device; none is available")
+        self.lib = load_library()
+        self.params = params
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self._c = params.to_c()
+        nbytes = int(self.lib.lbpc_workspace_bytes(ctypes.byref(self._c)))
+        if nbytes == 0:
+            s, msg = check_params(params)
+            raise LbpcError(s, msg)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self.stream = torch.cuda.current_stream(self.device) if stream is None else stream
+            ctx = ctypes.c_void_p()
+            s = self.lib.lbpc_create(ctypes.byref(self._c), ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                     ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(ctx))
+        if s != LBPC_OK:
+            raise LbpcError(s, "lbpc_create")
+        self.ctx = ctx
+        self.nx, self.ny = params.nx, params.ny
+
+    # -- helpers ------------------------------------------------------------------------------
+    def _raise(self, s, what):
+        if s != LBPC_OK:
+            raise LbpcError(s, f"{what}: {self.lib.lbpc_last_error(self.ctx).decode()}")
+
+    def _host(self, a):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(self.ny, self.nx))
+        return a
+
+    # -- API ----------------------------------------------------------------------------------
+    def init(self, rho, T, ux=None, uy=None):
+        """Equilibrium start from FP64 fields: numpy arrays (host) or CUDA tensors (device)."""
+        import torch
+
+        if isinstance(rho, torch.Tensor):
+            args = [x if x is None else x.to(device=self.device, dtype=torch.float64).contiguous() for x in (rho, T, ux, uy)]
+            ptrs = [ctypes.c_void_p(0) if x is None else ctypes.c_void_p(x.data_ptr()) for x in args]
+            self._keep = args
+            s = self.lib.lbpc_init(self.ctx, *ptrs, 1)
+        else:
+            args = [self._host(x) for x in (rho, T, ux, uy)]
+            ptrs = [ctypes.c_void_p(0) if x is None else _ptr(x) for x in args]
+            s = self.lib.lbpc_init(self.ctx, *ptrs, 0)
+        self._raise(s, "lbpc_init")
+
+    def step(self, n=1, sync=True):
+        s = (self.lib.lbpc_step if sync else self.lib.lbpc_step_async)(self.ctx, int(n))
+        self._raise(s, "lbpc_step")
+
+    def step_timed(self):
+        """One step; returns {kernel name: launch duration in ms} measured with CUDA events on the
+        context's stream."""
+        ms = (ctypes.c_float * 16)()
+        n = ctypes.c_int32()
+        self._raise(self.lib.lbpc_step_timed(self.ctx, ms, 16, ctypes.byref(n)), "lbpc_step_timed")
+        return {self.lib.lbpc_kernel_name(self.ctx, k).decode(): float(ms[k]) for k in range(n.value)}
+
+    def check(self):
+        self._raise(self.lib.lbpc_check(self.ctx), "lbpc_check")
+
+    def fields(self, device=False):
+        """(rho, ux, uy, T) of the current state as [ny][nx] FP64 numpy arrays (or CUDA tensors)."""
+        import torch
+
+        if device:
+            out = [torch.empty((self.ny, self.nx), dtype=torch.float64, device=self.device) for _ in range(4)]
+            s = self.lib.lbpc_fields(self.ctx, *[ctypes.c_void_p(t.data_ptr()) for t in out], 1)
+        else:
+            out = [np.empty((self.ny, self.nx)) for _ in range(4)]
+            s = self.lib.lbpc_fields(self.ctx, *[_ptr(a) for a in out], 0)
+        self._raise(s, "lbpc_fields")
+        return tuple(out)
+
+    def sums(self):
+        m, h = ctypes.c_double(), ctypes.c_double()
+        self._raise(self.lib.lbpc_sums(self.ctx, ctypes.byref(m), ctypes.byref(h)), "lbpc_sums")
+        return m.value, h.value
+
+    def populations(self):
+        f = np.empty((9, self.ny, self.nx))
+        g = np.empty((9, self.ny, self.nx))
+        self._raise(self.lib.lbpc_populations(self.ctx, _ptr(f), _ptr(g), 0), "lbpc_populations")
+        return f, g
+
+    @property
+    def step_count(self):
+        return int(self.lib.lbpc_step_count(self.ctx))
+
+    def last_error(self):
+        return self.lib.lbpc_last_error(self.ctx).decode()
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            self.lib.lbpc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_FLOW = {"periodic": PERIODIC, "wall": WALL, "pressure": PRESSURE}
+_TBC = {"none": T_NONE, "dirichlet": T_DIRICHLET}
+_LAM = {"const": LAMBDA_CONST, "rho_cv_chi": LAMBDA_RHO_CV_CHI}
+_MODEL = {"improved": IMPROVED, "compromised": COMPROMISED}
+
+
+def params_from_case(case: dict, prec: int = FP64) -> Params:
+    """Params from a workload dict (see paper_1709_04400_gb300.workloads)."""
+    return Params(
+        nx=case["nx"], ny=case["ny"], prec=prec, model=_MODEL[case.get("model", "improved")],
+        s_f=case["s_f"], s_g=case["s_g"], sigma=case["sigma"], lambda_mode=_LAM[case["lambda_mode"]],
+        lam=case.get("lam", 0.0), chi=case.get("chi", 0.06), cV=case["cV"], gx=case.get("gx", 0.0),
+        gy=case.get("gy", 0.0), buoyancy=case.get("buoyancy", False),
+        flow_bc=[_FLOW[k] for k in case["flow_bc"]], rho_bc=case.get("rho_bc", (0.0,) * 4),
+        t_bc=[_TBC[k] for k in case["t_bc"]], T_bc=case.get("T_bc", (0.0,) * 4), strip=case.get("strip"),
+        G_wall=case.get("G_wall", 0.0))

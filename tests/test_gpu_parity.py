@@ -1,0 +1,164 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Bar: FP64 storage and arithmetic within 1e-10 relative error on rho, u and T (max_i |a-b|/|b| for
+rho and T, ||a-b||_inf/||b||_inf for u, which vanishes pointwise); FP32 within 1e-4 on the same
+metrics. Grids are ragged (not multiples of the 256-thread block) and span many blocks."""
+
+import numpy as np
+import pytest
+
+from oracle import model
+from paper_1709_04400_gb300 import lbpc, workloads
+
+from .helpers import RL, RV, TC, TS, max_rel, norm_rel, oracle_params, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+
+    from paper_1709_04400_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def _gpu(case, rho, T, steps, prec=lbpc.FP64):
+    sim = lbpc.Simulation(lbpc.params_from_case(case, prec))
+    sim.init(rho, T)
+    sim.step(steps)
+    out = sim.fields()
+    f, g = sim.populations()
+    sums = sim.sums()
+    sim.close()
+    return out, f, g, sums
+
+
+def _errors(gpu, p, s):
+    r_o, ux_o, uy_o, T_o = model.fields(p, s)
+    r_g, ux_g, uy_g, T_g = gpu
+    return dict(rho=max_rel(r_g, r_o), T=max_rel(T_g, T_o), ux=norm_rel(ux_g, ux_o), uy=norm_rel(uy_g, uy_o))
+
+
+def _assert_within(err, tol):
+    bad = {k: v for k, v in err.items() if not v <= tol}
+    assert not bad, f"errors above {tol}: {err}"
+
+
+def test_mixed_boundaries_fp64():
+    """Wall + strip + pressure top + buoyancy + lambda = rho c_V chi + distinct thermal rates."""
+    case, rho, T = workloads.mixed_small(TC, RV, RL)
+    steps = 150
+    gpu, f, g, _ = _gpu(case, rho, T, steps)
+    p, s = run_oracle(case, rho, T, steps)
+    _assert_within(_errors(gpu, p, s), 1e-10)
+    assert np.max(np.abs(f - s.f)) / np.max(np.abs(s.f)) < 1e-10
+    assert np.max(np.abs(g - s.g)) / np.max(np.abs(s.g)) < 1e-10
+
+
+def test_compromised_model_fp64():
+    case, rho, T = workloads.mixed_small(TC, RV, RL, nx=33, ny=17)
+    case = dict(case, model="compromised")
+    gpu, *_ = _gpu(case, rho, T, 100)
+    p, s = run_oracle(case, rho, T, 100)
+    _assert_within(_errors(gpu, p, s), 1e-10)
+
+
+def test_wall_top_and_pressure_bottom_fp64():
+    """The mirrored boundary set: wall on y+, pressure on y-, adiabatic (no Dirichlet) top."""
+    case, rho, T = workloads.mixed_small(TC, RV, RL, nx=19, ny=23)
+    rho = rho[::-1].copy()
+    case = dict(case, flow_bc=("periodic", "periodic", "pressure", "wall"), rho_bc=(0, 0, RV, 0),
+                t_bc=("none", "none", "dirichlet", "none"), strip=None, gy=3e-5)
+    gpu, *_ = _gpu(case, rho, T, 100)
+    p, s = run_oracle(case, rho, T, 100)
+    _assert_within(_errors(gpu, p, s), 1e-10)
+
+
+def test_droplet_periodic_128_fp64_1000_steps():
+    """The 128 x 128 periodic droplet: 1000 steps, 1e-10 on rho, u, T (spec parity bar)."""
+    case, rho, T = workloads.droplet_periodic(TC, RV, RL)
+    gpu, _, _, (mass, heat) = _gpu(case, rho, T, 1000)
+    p, s = run_oracle(case, rho, T, 1000)
+    err = _errors(gpu, p, s)
+    _assert_within(err, 1e-10)
+    assert abs(mass - s.f.sum()) / s.f.sum() < 1e-12
+    assert abs(heat - s.g.sum()) / s.g.sum() < 1e-12
+
+
+@pytest.mark.parametrize("dT", [0.05, 0.1, 0.2])
+def test_droplet_evaporation_256_fp64(dT):
+    """The 256 x 256 evaporation case at full size, 200 steps (the oracle's share of the run)."""
+    case, rho, T = workloads.droplet_evaporation(TC, RV, RL, dT_ratio=dT)
+    gpu, *_ = _gpu(case, rho, T, 200)
+    p, s = run_oracle(case, rho, T, 200)
+    _assert_within(_errors(gpu, p, s), 1e-10)
+
+
+def test_heated_wall_fp32():
+    """The 300 x 400 heated-wall pool in FP32 storage and arithmetic against the FP64 oracle."""
+    case, rho, T = workloads.heated_wall(TC, RV, RL)
+    steps = 100
+    gpu, *_ = _gpu(case, rho, T, steps, prec=lbpc.FP32)
+    p, s = run_oracle(case, rho, T, steps)
+    _assert_within(_errors(gpu, p, s), 1e-4)
+
+
+def test_mass_conservation_gpu():
+    case, rho, T = workloads.droplet_periodic(TC, RV, RL, n=64, radius=12.0)
+    sim = lbpc.Simulation(lbpc.params_from_case(case))
+    sim.init(rho, T)
+    m0, _ = sim.sums()
+    sim.step(2000)
+    m1, _ = sim.sums()
+    sim.close()
+    assert abs(m1 - m0) / m0 < 1e-13
+
+
+def test_smallest_grid_and_zero_steps():
+    case, rho, T = workloads.mixed_small(TC, RV, RL, nx=2, ny=3)
+    gpu, *_ = _gpu(case, rho, T, 0)
+    p = oracle_params(case)
+    s = model.init_state(p, rho, T)
+    _assert_within(_errors(gpu, p, s), 1e-13)
+    gpu, *_ = _gpu(case, rho, T, 5)
+    s = model.run(p, s, 5)
+    _assert_within(_errors(gpu, p, s), 1e-10)
+
+
+def test_device_pointers_and_async_steps():
+    import torch
+
+    case, rho, T = workloads.mixed_small(TC, RV, RL)
+    sim = lbpc.Simulation(lbpc.params_from_case(case))
+    sim.init(torch.from_numpy(rho).cuda(), torch.from_numpy(T).cuda())
+    for _ in range(10):
+        sim.step(3, sync=False)
+    sim.check()
+    assert sim.step_count == 30
+    dev = [t.cpu().numpy() for t in sim.fields(device=True)]
+    host = sim.fields()
+    for a, b in zip(dev, host):
+        assert np.array_equal(a, b)
+    sim.close()
+    p, s = run_oracle(case, rho, T, 30)
+    _assert_within(_errors(host, p, s), 1e-10)
+
+
+def test_nonphysical_state_reported():
+    case, rho, T = workloads.droplet_periodic(TC, RV, RL, n=32, radius=8.0)
+    rho = rho.copy()
+    rho[7, 11] = 11.0  # beyond the EOS pole 1/b = 10.5
+    sim = lbpc.Simulation(lbpc.params_from_case(case))
+    sim.init(rho, T)
+    with pytest.raises(lbpc.LbpcError) as e:
+        sim.step(3)
+    assert e.value.status == lbpc.LBPC_ENONPHYS
+    assert "step 0, node (x=11, y=7)" in str(e.value)
+    with pytest.raises(lbpc.LbpcError) as e2:
+        sim.step(1)
+    assert e2.value.status == lbpc.LBPC_ESTATE
+    sim.fields()  # still readable
+    sim.close()

@@ -1,0 +1,93 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every symbol include/lbpc.h declares,
+and its host-side helpers (parameter validation, workspace sizing, EOS) behave. No GPU needed."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1709_04400_gb300 import build, lbpc
+
+from .helpers import RL, RV, TC, TS
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return lbpc.load_library()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "lbpc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbpc_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 16
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(lbpc.EXPORTED) == sorted(n for n in names)
+    assert lib.lbpc_version() == 1
+
+
+def test_struct_layout_matches_header():
+    # 16 int32 then 40 doubles: no padding, 384 bytes
+    assert ctypes.sizeof(lbpc.CParams) == 16 * 4 + (5 + 9 + 9 + 4 + 2 + 4 + 4 + 2) * 8
+    assert lbpc.CParams.a.offset == 64
+
+
+def test_check_params(lib):
+    ok = lbpc.Params(nx=32, ny=16)
+    assert lbpc.check_params(ok)[0] == lbpc.LBPC_OK
+    bad = [
+        dict(nx=1), dict(ny=0), dict(prec=7), dict(model=3),
+        dict(flow_bc=(lbpc.WALL, lbpc.WALL, 0, 0)),
+        dict(flow_bc=(0, 0, lbpc.WALL, 0)),
+        dict(flow_bc=(0, 0, lbpc.WALL, lbpc.PRESSURE)),  # pressure edge needs rho_bc > 0
+        dict(t_bc=(1, 0, 0, 0)),  # Dirichlet needs T_bc > 0
+        dict(strip=(3, 9, 0.1)),  # strip needs a Dirichlet y- edge
+        dict(s_g=(1.0,) * 8 + (2.0,)), dict(cV=0.0), dict(lam=-1.0), dict(b=0.0),
+    ]
+    for kw in bad:
+        p = lbpc.Params(**{**dict(nx=32, ny=16), **kw})
+        s, msg = lbpc.check_params(p)
+        assert s == lbpc.LBPC_EINVAL, (kw, msg)
+        assert lbpc.workspace_bytes(p) == 0
+    p = lbpc.Params(nx=32, ny=16, flow_bc=(0, 0, lbpc.WALL, lbpc.PRESSURE), rho_bc=(0, 0, 0, 0.4),
+                    t_bc=(0, 0, 1, 1), T_bc=(0, 0, 0.09, 0.09), strip=(10, 20, 0.12))
+    assert lbpc.check_params(p)[0] == lbpc.LBPC_OK
+
+
+def test_workspace_grows_with_grid(lib):
+    w1 = lbpc.workspace_bytes(lbpc.Params(nx=64, ny=64))
+    w2 = lbpc.workspace_bytes(lbpc.Params(nx=128, ny=128))
+    w3 = lbpc.workspace_bytes(lbpc.Params(nx=128, ny=128, prec=lbpc.FP32))
+    # FP64: 4 x 9 population planes + phi + 11 scratch planes = 48 planes of 8 bytes per node
+    assert 48 * 8 * 128 * 128 <= w2 < 48 * 8 * 128 * 128 + 64 * 1024
+    assert w2 > 3.9 * w1 and w3 < 0.55 * w2
+
+
+def test_eos_helpers_match_oracle(lib):
+    p = lbpc.Params(nx=8, ny=8)
+    Tc, pc = lbpc.eos_critical(p)
+    assert Tc == pytest.approx(TC, rel=1e-15)
+    rv, rl, ps = lbpc.coexistence(p, TS)
+    # equal fugacity (library) against equal area (oracle): two routes to the same coexistence
+    assert rv == pytest.approx(RV, rel=1e-11) and rl == pytest.approx(RL, rel=1e-11)
+    with pytest.raises(lbpc.LbpcError):
+        lbpc.coexistence(p, 1.01 * Tc)
+
+
+def test_simulation_refuses_without_gpu():
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(RuntimeError):
+        lbpc.Simulation(lbpc.Params(nx=8, ny=8))
