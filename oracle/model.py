@@ -24,11 +24,13 @@ READINGS (the paper is silent or delegates; every one is also listed in the desi
   * Isotropic differences: d_i X = 3 sum_a w_a X(x+e_a) e_ai, lap X = 6 sum_a w_a (X(x+e_a) - X(x)).
   * First step: phi(t - dt) := phi(t). rho_ave lags one step (step 0 uses the initial mean).
   * x is periodic. A non-periodic y edge is an on-node row: a no-slip wall (Zou-He, u = 0) or a
-    fixed-density edge (Zou-He, u_x = 0). Stencils that cross such an edge see ghost rows that copy
-    the edge row (zero gradient); for F_int a wall ghost has psi = 0 and instead adds the adsorption
-    force F_ads = -G_w psi(x) sum_a w_a s(x + e_a) e_a (s = 1 on the solid ghost row).
-  * A Dirichlet-T node gets g := M^{-1} m_eq(T_bc, v = 0) after streaming; a non-periodic edge
-    without Dirichlet T bounces back the unknown g (zero normal heat flux).
+    fixed-density edge (Zou-He, u_x = 0). Stencils that cross such an edge, F_int's included, see
+    ghost rows that copy the edge row (zero gradient), so a wall with G_w = 0 is neutral; at a wall
+    the adsorption force F_ads = -G_w psi(x) sum_a w_a s(x + e_a) e_a (s = 1 on the solid ghost row)
+    sets the wettability (G_w < 0 attracts liquid).
+  * A held temperature on a non-periodic y edge (wall rows, the heated strip) enters through the
+    unknown g by anti-bounce-back; without one those g bounce back (zero heat flux). A Dirichlet
+    ring inside a periodic domain resets its nodes to g := M^{-1} m_eq(T_bc, v = 0).
 
 Test hooks (never used by the GPU path): ``frozen_flow=(vx, vy)`` keeps f fixed and imposes a
 uniform v with F = 0; ``frozen_thermal=True`` keeps g fixed.
@@ -216,10 +218,8 @@ def macroscopic(p: OracleParams, s: OracleState):
         pse = _extend(psi, p, ghost="copy")
         solid = np.zeros_like(pse)
         if wall_lo:
-            pse[0, :] = 0.0
             solid[0, :] = 1.0
         if wall_hi:
-            pse[-1, :] = 0.0
             solid[-1, :] = 1.0
         wF = {1: 1.0 / 3.0, 2: 1.0 / 12.0}
         sx = sum(wF[L.EX[a] ** 2 + L.EY[a] ** 2] * _nb(pse, a) * L.EX[a] for a in range(1, 9))
@@ -336,25 +336,41 @@ def _heat_eq_at_rest(T, model):
     return L.from_moments(heat_meq(T, z, z, model))
 
 
+def _row_T(p: OracleParams, edge, n):
+    T = np.full(n, p.T_bc[edge])
+    if edge == 2 and p.strip is not None:
+        x0, x1, Ts = p.strip
+        T[x0:x1] = Ts
+    return T
+
+
 def heat_boundaries(p: OracleParams, g):
-    """Thermal boundary step (READING): bounce-back of the unknown g on non-periodic y edges, then
-    Dirichlet nodes g := M^{-1} m_eq(T_bc, 0): x edges first, then y edges, then the heated strip."""
-    if p.flow_bc[2] != "periodic":
-        g[2, 0], g[5, 0], g[6, 0] = g[4, 0].copy(), g[7, 0].copy(), g[8, 0].copy()
-        g[4, -1], g[7, -1], g[8, -1] = g[2, -1].copy(), g[5, -1].copy(), g[6, -1].copy()
+    """Thermal boundary step (READING; the paper states only which temperatures are held).
+
+    On a non-periodic y edge the unknown g (those streamed in from beyond the edge) are closed by
+    bounce-back: g_a = -g_opp(a) + 2 g_a^eq(T_bc, 0) when the edge holds T_bc (anti-bounce-back, so
+    heat enters through the wall), g_a = g_opp(a) otherwise (zero heat flux). Dirichlet edges of a
+    periodic axis (a ring of nodes inside a periodic domain) reset the node to g := M^{-1} m_eq(T_bc, 0):
+    x edges first, then y edges."""
     ny, nx = g.shape[1:]
+    if p.flow_bc[2] != "periodic":
+        for edge, row, unknown, known in ((2, 0, (2, 5, 6), (4, 7, 8)), (3, -1, (4, 7, 8), (2, 5, 6))):
+            if p.t_bc[edge] == "dirichlet":
+                geq = _heat_eq_at_rest(_row_T(p, edge, nx), p.model)
+                for a, b in zip(unknown, known):
+                    g[a, row] = -g[b, row] + 2.0 * geq[a]
+            else:
+                for a, b in zip(unknown, known):
+                    g[a, row] = g[b, row]
     if p.t_bc[0] == "dirichlet":
         g[:, :, 0] = _heat_eq_at_rest(np.full(ny, p.T_bc[0]), p.model)
     if p.t_bc[1] == "dirichlet":
         g[:, :, -1] = _heat_eq_at_rest(np.full(ny, p.T_bc[1]), p.model)
-    if p.t_bc[2] == "dirichlet":
-        Trow = np.full(nx, p.T_bc[2])
-        if p.strip is not None:
-            x0, x1, Ts = p.strip
-            Trow[x0:x1] = Ts
-        g[:, 0, :] = _heat_eq_at_rest(Trow, p.model)
-    if p.t_bc[3] == "dirichlet":
-        g[:, -1, :] = _heat_eq_at_rest(np.full(nx, p.T_bc[3]), p.model)
+    if p.flow_bc[2] == "periodic":
+        if p.t_bc[2] == "dirichlet":
+            g[:, 0, :] = _heat_eq_at_rest(_row_T(p, 2, nx), p.model)
+        if p.t_bc[3] == "dirichlet":
+            g[:, -1, :] = _heat_eq_at_rest(_row_T(p, 3, nx), p.model)
     return g
 
 

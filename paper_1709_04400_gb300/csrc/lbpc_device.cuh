@@ -161,19 +161,46 @@ template <class R> __device__ __forceinline__ void heat_meq(R T, R vx, R vy, int
   n[8] = R(0);
 }
 
-// Thermal boundary step: bounce-back of the unknown g on non-periodic y edges, then Dirichlet
-// nodes g := M^{-1} m_eq(T_bc, 0) (x edges, then y edges, then the heated strip).
+// Thermal boundary step. On a non-periodic y edge the unknown g are closed by bounce-back:
+// g_a = -g_opp(a) + 2 g_a^eq(T_bc, 0) where the edge holds T_bc (anti-bounce-back; heat enters through
+// the wall), g_a = g_opp(a) otherwise (zero heat flux). A Dirichlet edge of a periodic axis (a ring
+// inside a periodic domain) resets the node to g := M^{-1} m_eq(T_bc, 0): x edges, then y edges.
 template <class R> __device__ __forceinline__ void heat_closure(R g[9], const DevParams& P, int x, int y) {
   if (!P.yper) {
-    if (y == 0) { g[2] = g[4]; g[5] = g[7]; g[6] = g[8]; }
-    if (y == P.ny - 1) { g[4] = g[2]; g[7] = g[5]; g[8] = g[6]; }
+    if (y == 0) {
+      if (P.tbc[2]) {
+        const double Tb = (x >= P.strip_x0 && x < P.strip_x1) ? P.T_strip : P.T_bc[2];
+        R n[9], e[9];
+        heat_meq(R(Tb), R(0), R(0), P.model, n);
+        from_moments(n, e);
+        g[2] = R(2) * e[2] - g[4];
+        g[5] = R(2) * e[5] - g[7];
+        g[6] = R(2) * e[6] - g[8];
+      } else {
+        g[2] = g[4]; g[5] = g[7]; g[6] = g[8];
+      }
+    }
+    if (y == P.ny - 1) {
+      if (P.tbc[3]) {
+        R n[9], e[9];
+        heat_meq(R(P.T_bc[3]), R(0), R(0), P.model, n);
+        from_moments(n, e);
+        g[4] = R(2) * e[4] - g[2];
+        g[7] = R(2) * e[7] - g[5];
+        g[8] = R(2) * e[8] - g[6];
+      } else {
+        g[4] = g[2]; g[7] = g[5]; g[8] = g[6];
+      }
+    }
   }
   bool set = false;
   double Tb = 0.0;
   if (x == 0 && P.tbc[0]) { set = true; Tb = P.T_bc[0]; }
   if (x == P.nx - 1 && P.tbc[1]) { set = true; Tb = P.T_bc[1]; }
-  if (y == 0 && P.tbc[2]) { set = true; Tb = (x >= P.strip_x0 && x < P.strip_x1) ? P.T_strip : P.T_bc[2]; }
-  if (y == P.ny - 1 && P.tbc[3]) { set = true; Tb = P.T_bc[3]; }
+  if (P.yper) {
+    if (y == 0 && P.tbc[2]) { set = true; Tb = (x >= P.strip_x0 && x < P.strip_x1) ? P.T_strip : P.T_bc[2]; }
+    if (y == P.ny - 1 && P.tbc[3]) { set = true; Tb = P.T_bc[3]; }
+  }
   if (set) {
     R n[9];
     heat_meq(R(Tb), R(0), R(0), P.model, n);

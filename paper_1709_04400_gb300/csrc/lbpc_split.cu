@@ -106,11 +106,8 @@ __global__ void __launch_bounds__(BLOCK) k_force(Planes<R> pl, DevParams P, cons
   const R* __restrict__ psi = pl.p[P_PSI];
   R c[3][3];
   gather9(psi, P, x, y, c);
-  // F_int = -G psi(x) sum_a w(|e_a|^2) psi(x+e_a) e_a, w(1) = 1/3, w(2) = 1/12; a wall ghost has psi = 0.
-  if (!P.yper) {
-    if (y == 0 && P.ybc_lo == BC_WALL) c[0][0] = c[0][1] = c[0][2] = R(0);
-    if (y == P.ny - 1 && P.ybc_hi == BC_WALL) c[2][0] = c[2][1] = c[2][2] = R(0);
-  }
+  // F_int = -G psi(x) sum_a w(|e_a|^2) psi(x+e_a) e_a, w(1) = 1/3, w(2) = 1/12; ghost rows beyond a
+  // non-periodic edge copy the edge row, so a wall with G_wall = 0 is neutral.
   const R pc = psi[i];
   const R sx = (c[1][2] - c[1][0]) * R(1.0 / 3.0) + (c[2][2] - c[2][0] - c[0][0] + c[0][2]) * R(1.0 / 12.0);
   const R sy = (c[2][1] - c[0][1]) * R(1.0 / 3.0) + (c[2][2] + c[2][0] - c[0][0] - c[0][2]) * R(1.0 / 12.0);

@@ -29,7 +29,7 @@ BASE = dict(
 )
 # G_wall of the heated-wall case: a hydrophilic wall (fluid-solid attraction); the contact angle it
 # gives is not calibrated against the paper's 45 degrees.
-HEATED_WALL_G_WALL = -0.9
+HEATED_WALL_G_WALL = -0.2
 
 
 def droplet_periodic(Tc, rho_v, rho_l, n=128, radius=25.0, seed=inputs.SEED_BASE):
@@ -49,13 +49,14 @@ def droplet_evaporation(Tc, rho_v, rho_l, n=256, radius=40.0, dT_ratio=0.1):
 
 
 def heated_wall(Tc, rho_v, rho_l, nx=300, ny=400, strip_width=20, dT_strip_ratio=0.3, g=3e-5,
-                seed=inputs.SEED_BASE + 2):
+                seed=inputs.SEED_BASE + 2, top="pressure"):
+    """top = "pressure" holds the vapour density (the fixed-pressure top); "wall" closes the pool."""
     Ts = 0.86 * Tc
     rho, T = inputs.pool_with_noise(seed, nx, ny, 4.0, rho_l, rho_v, Ts, amp=1e-4)
     x0 = nx // 2 - strip_width // 2
-    case = dict(BASE, name=f"heated_wall_{nx}x{ny}", nx=nx, ny=ny, lambda_mode="rho_cv_chi", lam=0.0, chi=0.06,
-                gx=0.0, gy=-g, buoyancy=True,
-                flow_bc=("periodic", "periodic", "wall", "pressure"), rho_bc=(0.0, 0.0, 0.0, rho_v),
+    case = dict(BASE, name=f"heated_wall_{nx}x{ny}" + ("" if top == "pressure" else "_closed"), nx=nx, ny=ny,
+                lambda_mode="rho_cv_chi", lam=0.0, chi=0.06, gx=0.0, gy=-g, buoyancy=True,
+                flow_bc=("periodic", "periodic", "wall", top), rho_bc=(0.0, 0.0, 0.0, rho_v),
                 t_bc=("none", "none", "dirichlet", "dirichlet"), T_bc=(0.0, 0.0, Ts, Ts),
                 strip=(x0, x0 + strip_width, Ts + dT_strip_ratio * Tc), G_wall=HEATED_WALL_G_WALL)
     return case, rho, T
@@ -65,11 +66,11 @@ def mixed_small(Tc, rho_v, rho_l, nx=37, ny=29, seed=inputs.SEED_BASE + 5):
     """Small ragged grid with every boundary class: wall bottom with a strip, pressure top,
     buoyancy, lambda = rho c_V chi, non-default thermal rates (every term of Eqs. 45-55 active)."""
     Ts = 0.86 * Tc
-    rho, T = inputs.pool_with_noise(seed, nx, ny, 4.0, rho_l, rho_v, Ts, amp=0.05)
+    rho, T = inputs.pool_with_noise(seed, nx, ny, 4.0, rho_l, rho_v, Ts, amp=0.01)
     case = dict(BASE, name=f"mixed_{nx}x{ny}", nx=nx, ny=ny, lambda_mode="rho_cv_chi", lam=0.0, chi=0.06,
                 s_g=(1.0, 0.9, 1.05, 1.0, 1.2, 1.0, 1.2, 0.95, 0.85),
                 gx=1e-5, gy=-3e-5, buoyancy=True,
                 flow_bc=("periodic", "periodic", "wall", "pressure"), rho_bc=(0.0, 0.0, 0.0, rho_v),
                 t_bc=("none", "none", "dirichlet", "dirichlet"), T_bc=(0.0, 0.0, Ts, Ts),
-                strip=(10, 19, Ts + 0.2 * Tc), G_wall=-0.5)
+                strip=(nx // 4, nx // 2 + 1, Ts + 0.1 * Tc), G_wall=-0.2)
     return case, rho, T
