@@ -149,6 +149,11 @@ DevParams make_dev_params(const lbpc_params* p) {
   d.G_wall = p->G_wall;
   d.c3 = (1.0 - 0.5 * p->s_g[3]) * p->s_g[4];
   d.c5 = (1.0 - 0.5 * p->s_g[5]) * p->s_g[6];
+  d.inv_Tc = 1.0 / d.Tc;
+  for (int k = 0; k < 9; ++k) d.hf[k] = 1.0 - 0.5 * p->s_f[k];
+  d.qG2 = d.qcoef * p->G * p->G;
+  d.inv_cV = 1.0 / p->cV;
+  d.psi_scale = 2.0 / p->G;
   return d;
 }
 

@@ -37,6 +37,12 @@ struct DevParams {
   double lambda, chi, cV, kdiff;  // kdiff = (1/s_g3 - 1/2) c_s^2
   double gx, gy, G_wall;
   double c3, c5;     // (1 - s3/2) s4, (1 - s5/2) s6 of Eqs. 54-55
+  // constants folded on the host
+  double inv_Tc;     // 1 / T_c
+  double hf[9];      // 1 - s_f[k]/2, the forcing weights of (I - Lambda/2) S_F
+  double qG2;        // qcoef * G^2: Q = qcoef |F_int|^2 / psi^2 = qcoef G^2 |sum_a w psi e|^2
+  double inv_cV;     // 1 / c_V
+  double psi_scale;  // 2 / G: psi^2 = (2/G) (p - rho c_s^2)
 };
 
 template <class S> __device__ __forceinline__ double ld(const S* p) { return (double)__ldg(p); }
@@ -84,13 +90,20 @@ template <class R> __device__ __forceinline__ void from_moments(const R m[9], R 
 // Peng-Robinson EOS (Eq. 56) and (dp/dT)_rho
 // ------------------------------------------------------------------------------------------------
 template <class R> __device__ __forceinline__ void eos(R rho, R T, const DevParams& P, R& p, R& dpdT) {
-  const R sq = sqrt(T / R(P.Tc));                   // sqrt(T / T_c)
+  // theta(T) = [1 + kappa (1 - sqrt(T/T_c))]^2 and d theta/dT = -kappa [..] / sqrt(T T_c); one rsqrt
+  // gives both sqrt(T/T_c) = t rsqrt(t) and 1/sqrt(T T_c) = rsqrt(t) / T_c with t = T/T_c.
+  const R t = T * R(P.inv_Tc);
+  const R rs = rsqrt(t);
+  const R sq = t * rs;
   const R th1 = R(1) + R(P.kappa) * (R(1) - sq);
   const R theta = th1 * th1;
-  const R dtheta = -R(P.kappa) * th1 / (sq * R(P.Tc));  // d theta/dT = -kappa th1 / sqrt(T T_c)
+  const R dtheta = -R(P.kappa) * th1 * rs * R(P.inv_Tc);
+  // 1/(1 - b rho) and 1/(1 + 2 b rho - b^2 rho^2) from one reciprocal of their product
   const R br = R(P.b) * rho;
-  const R inv1 = R(1) / (R(1) - br);
-  const R inv2 = R(1) / (R(1) + R(2) * br - br * br);
+  const R d1 = R(1) - br;
+  const R d2 = R(1) + R(2) * br - br * br;
+  const R r12 = R(1) / (d1 * d2);
+  const R inv1 = d2 * r12, inv2 = d1 * r12;
   const R r2 = rho * rho;
   p = rho * R(P.R) * T * inv1 - R(P.a) * theta * r2 * inv2;
   dpdT = rho * R(P.R) * inv1 - R(P.a) * dtheta * r2 * inv2;
@@ -227,20 +240,24 @@ template <class R>
 __device__ __forceinline__ void collide_flow(R f[9], R rho, R vx, R vy, R Fx, R Fy, R Q, const DevParams& P) {
   R m[9];
   to_moments(f, m);
-  const R v2 = vx * vx + vy * vy;
+  const R vxx = vx * vx, vyy = vy * vy;
+  const R v2 = vxx + vyy;
   const R vF = vx * Fx + vy * Fy;
+  // conserved moments: m0* = m0 (S_F,0 = 0, m0_eq = rho) and j* = j + F whatever s_j (m_eq,3 = j + F/2)
+  m[3] += Fx;
+  m[5] += Fy;
   R meq[9], SF[9];
-  meq[0] = rho;                       SF[0] = R(0);
   meq[1] = rho * (R(-2) + R(3) * v2); SF[1] = R(6) * vF + Q;
   meq[2] = rho * (R(1) - R(3) * v2);  SF[2] = R(-6) * vF - Q;
-  meq[3] = rho * vx;                  SF[3] = Fx;
   meq[4] = -rho * vx;                 SF[4] = -Fx;
-  meq[5] = rho * vy;                  SF[5] = Fy;
   meq[6] = -rho * vy;                 SF[6] = -Fy;
-  meq[7] = rho * (vx * vx - vy * vy); SF[7] = R(2) * (vx * Fx - vy * Fy);
+  meq[7] = rho * (vxx - vyy);         SF[7] = R(2) * (vx * Fx - vy * Fy);
   meq[8] = rho * vx * vy;             SF[8] = vx * Fy + vy * Fx;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) m[k] = m[k] - R(P.s_f[k]) * (m[k] - meq[k]) + (R(1) - R(0.5) * R(P.s_f[k])) * SF[k];
+  for (int k = 1; k < 9; ++k) {
+    if (k == 3 || k == 5) continue;
+    m[k] = m[k] - R(P.s_f[k]) * (m[k] - meq[k]) + R(P.hf[k]) * SF[k];
+  }
   from_moments(m, f);
 }
 
@@ -251,9 +268,9 @@ template <class R> __device__ __forceinline__ void collide_heat(R g[9], R T, R v
   to_moments(g, n);
   heat_meq(T, vx, vy, P.model, neq);
   R ns[9];
+  ns[0] = n[0] + S0;  // n0_eq = T = n0: the relaxation leaves the zeroth moment, the source adds S0
 #pragma unroll
-  for (int k = 0; k < 9; ++k) ns[k] = n[k] - R(P.s_g[k]) * (n[k] - neq[k]);
-  ns[0] += S0;
+  for (int k = 1; k < 9; ++k) ns[k] = n[k] - R(P.s_g[k]) * (n[k] - neq[k]);
   if (P.model == 0) {
     ns[3] += R(P.c3) * (n[4] - neq[4]);
     ns[5] += R(P.c5) * (n[6] - neq[6]);

@@ -15,10 +15,10 @@
 
 namespace lbpc {
 
-constexpr int BLOCK = 256;
+constexpr int BLOCK = 64;  // small blocks spread small grids evenly over the 152 SMs
 
 // Planes of the split path's scratch (type R, N nodes each).
-enum { P_RHO = 0, P_T, P_PSI, P_JX, P_JY, P_DPDT, P_VX, P_VY, P_FX, P_FY, P_Q, NPLANES };
+enum { P_RHO = 0, P_T, P_PSI, P_JX, P_JY, P_DPDT, P_IRHO, P_VX, P_VY, P_FX, P_FY, P_Q, NPLANES };
 
 template <class R> struct Planes {
   R* p[NPLANES];
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(BLOCK) k_macro(const S* __restrict__ fsrc, con
     const R T = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
     R p, dpdT;
     eos(rho, T, P, p, dpdT);
-    const R psi2 = R(2) * (p - rho * R(1.0 / 3.0)) / R(P.G);
+    const R psi2 = R(P.psi_scale) * (p - rho * R(1.0 / 3.0));
     const int bad = classify(rho, T, psi2, P);
     if (bad) report(status, step, x, y, bad);
     pl.p[P_RHO][i] = rho;
@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(BLOCK) k_macro(const S* __restrict__ fsrc, con
     pl.p[P_JX][i] = jx;
     pl.p[P_JY][i] = jy;
     pl.p[P_DPDT][i] = dpdT;
+    pl.p[P_IRHO][i] = R(1) / rho;
     rho_d = (double)rho;
   }
   if (do_partials) {
@@ -124,12 +125,13 @@ __global__ void __launch_bounds__(BLOCK) k_force(Planes<R> pl, DevParams P, cons
     Fx += dr * R(P.gx);
     Fy += dr * R(P.gy);
   }
-  const R inv_rho = R(1) / rho;
+  const R inv_rho = pl.p[P_IRHO][i];
   pl.p[P_VX][i] = (pl.p[P_JX][i] + R(0.5) * Fx) * inv_rho;
   pl.p[P_VY][i] = (pl.p[P_JY][i] + R(0.5) * Fy) * inv_rho;
   pl.p[P_FX][i] = Fx;
   pl.p[P_FY][i] = Fy;
-  pl.p[P_Q][i] = R(P.qcoef) * (Fix * Fix + Fiy * Fiy) / (pc * pc);
+  // sigma term Q = qcoef |F_int|^2 / psi^2 = qcoef G^2 (sx^2 + sy^2): psi^2 cancels
+  pl.p[P_Q][i] = R(P.qG2) * (sx * sx + sy * sy);
 }
 
 template <class S, class R>
@@ -153,7 +155,7 @@ __global__ void __launch_bounds__(BLOCK) k_collide(const S* __restrict__ fsrc, c
   gather9(pl.p[P_VY], P, x, y, c);
   divv += d_y(c);
   const R rcv = rho * R(P.cV);
-  const R inv_rcv = R(1) / rcv;
+  const R inv_rcv = pl.p[P_IRHO][i] * R(P.inv_cV);
   R div_lam_gradT;
   if (P.lambda_mode == 0) {
     div_lam_gradT = R(P.lambda) * lapT;
