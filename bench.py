@@ -39,6 +39,7 @@ def parse():
     ap.add_argument("--n", type=int, default=0, help="grid side (0 = the workload's own size)")
     ap.add_argument("--dT", type=float, default=0.1, help="superheat dT / T_c of the evaporation case")
     ap.add_argument("--prec", default="", choices=["", "fp64", "fp32"])
+    ap.add_argument("--path", default="auto", choices=["auto", "split", "fused"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -144,12 +145,17 @@ def cpu_baseline(case, rho, T, budget_s=12.0):
             "sample": f"{n} oracle steps of the {case['nx']}x{case['ny']} workload ({dt:.1f} s, numpy FP64, 1 thread)"}
 
 
-# Algorithmic traffic of the collide kernel per node: pull 9 f + 9 g, write 9 f* + 9 g*, read/write
-# phi_prev, read the centre of 8 scratch planes (rho, T, vx, vy, Fx, Fy, Q, dp/dT); the neighbour
-# reads of T, vx, vy (and rho) are served by L1/L2 and not counted.
-def collide_bytes_per_node(prec_bytes, lambda_rho):
-    planes = 8 + (0 if not lambda_rho else 0)
-    return prec_bytes * (18 + 18 + 2 + planes)
+# Algorithmic HBM traffic per node and step of the fused kernel: read 9 f + 9 g, write 9 f* + 9 g*,
+# read and write phi_prev (152 B in FP32, 304 B in FP64).
+def fused_bytes_per_node(prec_bytes):
+    return prec_bytes * (18 + 18 + 2)
+
+
+# Algorithmic traffic of the split collide kernel per node: pull 9 f + 9 g, write 9 f* + 9 g*,
+# read/write phi_prev, read the centre of 9 scratch planes (rho, T, 1/rho, vx, vy, Fx, Fy, Q, dp/dT);
+# the neighbour reads of T, vx, vy (and rho) are served by L1/L2 and not counted.
+def collide_bytes_per_node(prec_bytes):
+    return prec_bytes * (18 + 18 + 2 + 9)
 
 
 # Algorithmic FP64 operations of the collide kernel per node (each add, subtract, multiply, divide and
@@ -182,7 +188,9 @@ def run_native(args):
         if ws > 1:
             dist.barrier()
 
+    path = {"auto": lbpc.PATH_AUTO, "split": lbpc.PATH_SPLIT, "fused": lbpc.PATH_FUSED}[args.path]
     sim = lbpc.Simulation(params)
+    sim.set_path(path)
     sim.init(rho, T)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     stream = sim.stream
@@ -226,21 +234,28 @@ def run_native(args):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    if prec == lbpc.FP64:
+    pb = 8 if prec == lbpc.FP64 else 4
+    peak_bw = float(peaks.get("hbm_gbs", 6800.0))
+    bw_src = "MEASURED_PEAKS.json hbm_gbs (burst copy)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
+    if prec == lbpc.FP64 and "k_collide" in avg:
         flops = COLLIDE_FLOPS[case["lambda_mode"]] * N
         achieved = flops / (avg["k_collide"] / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": "k_collide", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
                 "frac": achieved / 1.25, "traffic": None,
-                "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s, profiling recipe)",
-                "top_kernel": top}
+                "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s, profiling recipe); 1.20 measured FMA",
+                "flops_per_node": COLLIDE_FLOPS[case["lambda_mode"]], "top_kernel": top}
+    elif "k_fused" in avg:
+        bytes_ = fused_bytes_per_node(pb) * N
+        achieved = bytes_ / (avg["k_fused"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": "k_fused", "achieved": achieved, "peak": peak_bw, "unit": "GB/s",
+                "frac": achieved / peak_bw, "traffic": None, "peak_source": bw_src,
+                "bytes_per_node": fused_bytes_per_node(pb), "top_kernel": top}
     else:
-        bytes_ = collide_bytes_per_node(4, case["lambda_mode"] == "rho_cv_chi") * N
+        bytes_ = collide_bytes_per_node(pb) * N
         achieved = bytes_ / (avg["k_collide"] / 1e3) / 1e9
-        peak = float(peaks.get("hbm_gbs", 6800.0))
-        roof = {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6.8 TB/s",
-                "top_kernel": top}
+        roof = {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak_bw, "unit": "GB/s",
+                "frac": achieved / peak_bw, "traffic": None, "peak_source": bw_src,
+                "bytes_per_node": collide_bytes_per_node(pb), "top_kernel": top}
 
     e2e = None
     if not args.no_e2e:
@@ -250,6 +265,7 @@ def run_native(args):
         h_rho = torch.from_numpy(np.ascontiguousarray(rho)).pin_memory().numpy()
         h_T = torch.from_numpy(np.ascontiguousarray(T)).pin_memory().numpy()
         sim2 = lbpc.Simulation(params)
+        sim2.set_path(path)
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -284,7 +300,7 @@ def run_native(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == lbpc.FP64 else "f32", "data": "synthetic",
             "config": {"workload": case["name"], "nx": case["nx"], "ny": case["ny"], "nodes": N,
-                       "storage": prec_name, "parallelism": f"replicas{ws}",
+                       "storage": prec_name, "parallelism": f"replicas{ws}", "path": args.path,
                        "l2": "flushed before every timed step (512 MiB write); each step timed with CUDA events",
                        "wall_ms_per_step": wall * 1e3 / args.steps},
             "roofline": roof, "cpu_baseline": base, "e2e": e2e,

@@ -140,6 +140,14 @@ lbpc_status lbpc_step_timed(lbpc_ctx* c, float* kernel_ms, int32_t max_kernels, 
 /* Name of kernel k of the step as lbpc_step_timed orders them ("" if k is out of range). */
 const char* lbpc_kernel_name(const lbpc_ctx* c, int32_t k);
 
+/* Kernel organisation of lbpc_step. LBPC_PATH_SPLIT: three node-parallel kernels per step with
+ * scratch planes (each EOS evaluated once per node; the faster choice when FP64 arithmetic bounds
+ * the step). LBPC_PATH_FUSED: one kernel per step over shared-memory tiles (populations read once
+ * and written once; the faster choice when HBM bounds the step). LBPC_PATH_AUTO (default): split
+ * for LBPC_FP64, fused for LBPC_FP32. Both compute the same step. */
+typedef enum { LBPC_PATH_AUTO = 0, LBPC_PATH_SPLIT = 1, LBPC_PATH_FUSED = 2 } lbpc_path;
+lbpc_status lbpc_set_path(lbpc_ctx* c, int32_t path);
+
 /* Synchronise the stream and check the device status word. */
 lbpc_status lbpc_check(lbpc_ctx* c);
 

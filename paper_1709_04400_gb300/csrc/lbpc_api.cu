@@ -23,6 +23,7 @@ struct lbpc_ctx {
   cudaStream_t stream;
   SplitBuffers buf;
   int cur;              // buffer holding the current state
+  int path;             // lbpc_path
   long long step;
   int initialised;
   cudaEvent_t ev[8];    // created on first lbpc_step_timed
@@ -365,13 +366,37 @@ LBPC_API lbpc_status lbpc_init(lbpc_ctx* c, const double* rho, const double* T, 
   return LBPC_OK;
 }
 
+static bool use_fused(const lbpc_ctx* c) {
+  return c->path == LBPC_PATH_FUSED || (c->path == LBPC_PATH_AUTO && c->p.prec == LBPC_FP32);
+}
+
+static cudaError_t launch_step(lbpc_ctx* c, cudaEvent_t* ev) {
+  return use_fused(c) ? lbpc::fused_step(c->buf, c->dp, c->p.prec, c->cur, c->step, c->stream, ev)
+                      : lbpc::split_step(c->buf, c->dp, c->p.prec, c->cur, c->step, c->stream, ev);
+}
+
+static int step_kernel_count(const lbpc_ctx* c) {
+  return use_fused(c) ? (c->dp.buoyancy ? 2 : 1) : lbpc::split_kernel_count(c->dp);
+}
+
+static const char* step_kernel_name(const lbpc_ctx* c, int k) {
+  if (use_fused(c)) return k == 0 ? "k_fused" : (k == 1 ? "k_finish" : "");
+  return lbpc::split_kernel_name(k);
+}
+
+LBPC_API lbpc_status lbpc_set_path(lbpc_ctx* c, int32_t path) {
+  if (!c || path < LBPC_PATH_AUTO || path > LBPC_PATH_FUSED) return LBPC_EINVAL;
+  c->path = path;
+  return LBPC_OK;
+}
+
 LBPC_API lbpc_status lbpc_step_async(lbpc_ctx* c, int64_t n) {
   if (!c || n < 0) return LBPC_EINVAL;
   if (c->err != LBPC_OK) return LBPC_ESTATE;
   if (!c->initialised) return fail(c, LBPC_ESTATE, "lbpc_step before lbpc_init");
   DeviceGuard g(c->device);
   for (int64_t k = 0; k < n; ++k) {
-    CU(c, lbpc::split_step(c->buf, c->dp, c->p.prec, c->cur, c->step, c->stream), "lbpc_step launch");
+    CU(c, launch_step(c, nullptr), "lbpc_step launch");
     c->cur ^= 1;
     ++c->step;
   }
@@ -415,8 +440,8 @@ LBPC_API lbpc_status lbpc_step_timed(lbpc_ctx* c, float* kernel_ms, int32_t max_
     for (int k = 0; k < 8; ++k) CU(c, cudaEventCreate(&c->ev[k]), "lbpc_step_timed event create");
     c->have_events = 1;
   }
-  const int nk = lbpc::split_kernel_count(c->dp);
-  CU(c, lbpc::split_step(c->buf, c->dp, c->p.prec, c->cur, c->step, c->stream, c->ev), "lbpc_step_timed launch");
+  const int nk = step_kernel_count(c);
+  CU(c, launch_step(c, c->ev), "lbpc_step_timed launch");
   c->cur ^= 1;
   ++c->step;
   CU(c, cudaEventSynchronize(c->ev[nk]), "lbpc_step_timed sync");
@@ -430,8 +455,8 @@ LBPC_API lbpc_status lbpc_step_timed(lbpc_ctx* c, float* kernel_ms, int32_t max_
 }
 
 LBPC_API const char* lbpc_kernel_name(const lbpc_ctx* c, int32_t k) {
-  if (!c || k < 0 || k >= lbpc::split_kernel_count(c->dp)) return "";
-  return lbpc::split_kernel_name(k);
+  if (!c || k < 0 || k >= step_kernel_count(c)) return "";
+  return step_kernel_name(c, k);
 }
 
 LBPC_API lbpc_status lbpc_fields(lbpc_ctx* c, double* rho, double* ux, double* uy, double* T, int on_device) {

@@ -1,0 +1,242 @@
+// Fused form of the coupled step: one kernel per time step, one CTA per TX x TY tile.
+//
+// The collide at a node needs v and T on its 1-ring (div v, grad T, lap T), v needs F on that ring,
+// F needs psi on the 2-ring, psi needs rho and T there, and those need the pulled populations of the
+// 2-ring. A CTA therefore works in three shared-memory stages:
+//   1. tile + 2 ring: pull-stream + closures, moments rho, j, T and psi (the EOS) -> smem;
+//      the tile's own nodes keep their 18 pulled populations in registers;
+//   2. tile + 1 ring: F = F_int + F_ads + F_b and v = (j + F/2)/rho -> smem (tile nodes keep F, Q);
+//   3. tile: isotropic grad T, lap T, grad rho, div v, the source phi and S0, both MRT collisions,
+//      store f*, g* and phi.
+// HBM sees the populations read once and written once plus phi (the algorithmic 152 B/node in FP32);
+// the ring re-reads of neighbouring tiles' populations are served by L2. Ghost rows beyond a
+// non-periodic y edge copy the edge row (moments, psi and, through the clamped stencil, F and v).
+#include "lbpc_device.cuh"
+#include "lbpc_internal.h"
+
+namespace lbpc {
+
+namespace {
+
+__device__ __forceinline__ int wrap_any(int x, int n) {
+  x %= n;
+  return x < 0 ? x + n : x;
+}
+
+// Domain row for region row offset: wraps when y is periodic, else clamps to the edge row.
+__device__ __forceinline__ int row_of(const DevParams& P, int y) {
+  if (P.yper) return wrap_any(y, P.ny);
+  return y < 0 ? 0 : (y >= P.ny ? P.ny - 1 : y);
+}
+
+}  // namespace
+
+template <class S, class R, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY) k_fused(const S* __restrict__ fsrc, const S* __restrict__ gsrc,
+                                                   S* __restrict__ fdst, S* __restrict__ gdst,
+                                                   R* __restrict__ phi_prev, DevParams P, long long step, int first,
+                                                   const double* __restrict__ rho_ave, double* __restrict__ partials,
+                                                   long long* __restrict__ status) {
+  constexpr int RX = TX + 4, RY = TY + 4;  // stage-1 region (tile + 2)
+  constexpr int VX = TX + 2, VY = TY + 2;  // stage-2 region (tile + 1)
+  constexpr int NT = TX * TY;
+  __shared__ R s_rho[RY][RX], s_T[RY][RX], s_psi[RY][RX], s_jx[RY][RX], s_jy[RY][RX];
+  __shared__ R s_vx[VY][VX], s_vy[VY][VX];
+  __shared__ double s_red[NT / 32];
+
+  const int t = threadIdx.x;
+  const int tx = t % TX, ty = t / TX;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool active = gx < P.nx && gy < P.ny;
+  const int mx = wrap_any(gx, P.nx), my = row_of(P, gy);
+
+  // ---- stage 1a: own node (kept in registers) ----
+  R f[9], g[9];
+  pull_closed<S, R>(fsrc, gsrc, P, mx, my, f, g);
+  R rho, T, p, dpdT;
+  {
+    rho = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+    const R jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
+    const R jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
+    T = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
+    eos(rho, T, P, p, dpdT);
+    const R psi2 = R(P.psi_scale) * (p - rho * R(1.0 / 3.0));
+    if (active) {
+      const int bad = classify(rho, T, psi2, P);
+      if (bad) report(status, step, gx, gy, bad);
+    }
+    s_rho[ty + 2][tx + 2] = rho;
+    s_T[ty + 2][tx + 2] = T;
+    s_psi[ty + 2][tx + 2] = sqrt(fmax(psi2, R(0)));
+    s_jx[ty + 2][tx + 2] = jx;
+    s_jy[ty + 2][tx + 2] = jy;
+  }
+  // ---- stage 1b: the 2-wide ring around the tile ----
+  constexpr int RING1 = RX * RY - NT;
+  for (int r = t; r < RING1; r += NT) {
+    int hx, hy;
+    if (r < 2 * RX) {                       // two rows below
+      hx = r % RX; hy = r / RX;
+    } else if (r < 4 * RX) {                // two rows above
+      hx = (r - 2 * RX) % RX; hy = TY + 2 + (r - 2 * RX) / RX;
+    } else {                                // two columns left and right of the tile rows
+      const int q = r - 4 * RX;
+      hy = 2 + q / 4;
+      const int c = q % 4;
+      hx = c < 2 ? c : TX + c;
+    }
+    const int x = wrap_any(x0 + hx - 2, P.nx), y = row_of(P, y0 + hy - 2);
+    R fr[9], gr[9];
+    pull_closed<S, R>(fsrc, gsrc, P, x, y, fr, gr);
+    const R rr = fr[0] + fr[1] + fr[2] + fr[3] + fr[4] + fr[5] + fr[6] + fr[7] + fr[8];
+    const R Tr = gr[0] + gr[1] + gr[2] + gr[3] + gr[4] + gr[5] + gr[6] + gr[7] + gr[8];
+    R pr, dr;
+    eos(rr, Tr, P, pr, dr);
+    const R psi2 = R(P.psi_scale) * (pr - rr * R(1.0 / 3.0));
+    s_rho[hy][hx] = rr;
+    s_T[hy][hx] = Tr;
+    s_psi[hy][hx] = sqrt(fmax(psi2, R(0)));
+    s_jx[hy][hx] = fr[1] - fr[3] + fr[5] - fr[6] - fr[7] + fr[8];
+    s_jy[hy][hx] = fr[2] - fr[4] + fr[5] + fr[6] - fr[7] - fr[8];
+  }
+  if (P.buoyancy) {
+    const double sr = block_sum<NT>(active ? (double)rho : 0.0, s_red);
+    if (t == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = sr;
+  } else {
+    __syncthreads();
+  }
+
+  // ---- stage 2: F and v on tile + 1 ----
+  // F at stage-2 position (vx_, vy_) of the domain node (x, y); the stencil rows come from the clamped
+  // node's own region rows so a ghost position reproduces the edge node exactly.
+  const R rho_ref = P.buoyancy ? R(*rho_ave) : R(0);
+  auto force_at = [&](int hx, int hy, int y, R& Fx, R& Fy, R& Q, R& vx, R& vy) {
+    // hx, hy: stage-1 region coordinates of the node whose F is computed
+    const R c00 = s_psi[hy - 1][hx - 1], c01 = s_psi[hy - 1][hx], c02 = s_psi[hy - 1][hx + 1];
+    const R c10 = s_psi[hy][hx - 1], c12 = s_psi[hy][hx + 1];
+    const R c20 = s_psi[hy + 1][hx - 1], c21 = s_psi[hy + 1][hx], c22 = s_psi[hy + 1][hx + 1];
+    const R pc = s_psi[hy][hx];
+    const R sx = (c12 - c10) * R(1.0 / 3.0) + (c22 - c20 - c00 + c02) * R(1.0 / 12.0);
+    const R sy = (c21 - c01) * R(1.0 / 3.0) + (c22 + c20 - c00 - c02) * R(1.0 / 12.0);
+    Fx = -R(P.G) * pc * sx;
+    Fy = -R(P.G) * pc * sy;
+    if (!P.yper) {
+      if (y == 0 && P.ybc_lo == BC_WALL) Fy += R(0.5) * R(P.G_wall) * pc;
+      if (y == P.ny - 1 && P.ybc_hi == BC_WALL) Fy -= R(0.5) * R(P.G_wall) * pc;
+    }
+    const R rr = s_rho[hy][hx];
+    if (P.buoyancy) {
+      const R d = rr - rho_ref;
+      Fx += d * R(P.gx);
+      Fy += d * R(P.gy);
+    }
+    Q = R(P.qG2) * (sx * sx + sy * sy);
+    const R ir = R(1) / rr;
+    vx = (s_jx[hy][hx] + R(0.5) * Fx) * ir;
+    vy = (s_jy[hy][hx] + R(0.5) * Fy) * ir;
+  };
+  // region row (stage-1 coordinates) holding the clamped domain row of stage-1 row hy
+  auto clamp_hy = [&](int hy) {
+    if (P.yper) return hy;
+    const int y = y0 + hy - 2;
+    if (y < 0) return hy - y;                 // row of y = 0
+    if (y >= P.ny) return hy - (y - (P.ny - 1));  // row of y = ny - 1
+    return hy;
+  };
+  R Fx, Fy, Q, vx, vy;
+  {
+    const int hy = clamp_hy(ty + 2);
+    force_at(tx + 2, hy, my, Fx, Fy, Q, vx, vy);
+    s_vx[ty + 1][tx + 1] = vx;
+    s_vy[ty + 1][tx + 1] = vy;
+  }
+  constexpr int RING2 = VX * VY - NT;
+  for (int r = t; r < RING2; r += NT) {
+    int hx, hy;  // stage-2 coordinates
+    if (r < VX) {
+      hx = r; hy = 0;
+    } else if (r < 2 * VX) {
+      hx = r - VX; hy = TY + 1;
+    } else {
+      const int q = r - 2 * VX;
+      hy = 1 + q / 2;
+      hx = (q % 2) ? TX + 1 : 0;
+    }
+    const int y1 = clamp_hy(hy + 1);
+    const int ydom = row_of(P, y0 + hy - 1);
+    R a, b, c, vxr, vyr;
+    force_at(hx + 1, y1, ydom, a, b, c, vxr, vyr);
+    s_vx[hy][hx] = vxr;
+    s_vy[hy][hx] = vyr;
+  }
+  __syncthreads();
+
+  // ---- stage 3: gradients, source, collisions on the tile ----
+  if (!active) return;
+  const int hx = tx + 2, hy = ty + 2;  // stage-1 coordinates of the own node
+  const R gTx = (s_T[hy][hx + 1] - s_T[hy][hx - 1]) * R(1.0 / 3.0) +
+                (s_T[hy + 1][hx + 1] - s_T[hy + 1][hx - 1] - s_T[hy - 1][hx - 1] + s_T[hy - 1][hx + 1]) * R(1.0 / 12.0);
+  const R gTy = (s_T[hy + 1][hx] - s_T[hy - 1][hx]) * R(1.0 / 3.0) +
+                (s_T[hy + 1][hx + 1] + s_T[hy + 1][hx - 1] - s_T[hy - 1][hx - 1] - s_T[hy - 1][hx + 1]) * R(1.0 / 12.0);
+  const R lapT = (s_T[hy][hx + 1] + s_T[hy][hx - 1] + s_T[hy + 1][hx] + s_T[hy - 1][hx] - R(4) * T) * R(2.0 / 3.0) +
+                 (s_T[hy + 1][hx + 1] + s_T[hy + 1][hx - 1] + s_T[hy - 1][hx - 1] + s_T[hy - 1][hx + 1] - R(4) * T) *
+                     R(1.0 / 6.0);
+  const int ux = tx + 1, uy = ty + 1;  // stage-2 coordinates
+  const R divv = (s_vx[uy][ux + 1] - s_vx[uy][ux - 1]) * R(1.0 / 3.0) +
+                 (s_vx[uy + 1][ux + 1] - s_vx[uy + 1][ux - 1] - s_vx[uy - 1][ux - 1] + s_vx[uy - 1][ux + 1]) * R(1.0 / 12.0) +
+                 (s_vy[uy + 1][ux] - s_vy[uy - 1][ux]) * R(1.0 / 3.0) +
+                 (s_vy[uy + 1][ux + 1] + s_vy[uy + 1][ux - 1] - s_vy[uy - 1][ux - 1] - s_vy[uy - 1][ux + 1]) * R(1.0 / 12.0);
+  const R rcv = rho * R(P.cV);
+  const R inv_rcv = R(1) / rcv;
+  R div_lam_gradT;
+  if (P.lambda_mode == 0) {
+    div_lam_gradT = R(P.lambda) * lapT;
+  } else {
+    const R grx = (s_rho[hy][hx + 1] - s_rho[hy][hx - 1]) * R(1.0 / 3.0) +
+                  (s_rho[hy + 1][hx + 1] - s_rho[hy + 1][hx - 1] - s_rho[hy - 1][hx - 1] + s_rho[hy - 1][hx + 1]) * R(1.0 / 12.0);
+    const R gry = (s_rho[hy + 1][hx] - s_rho[hy - 1][hx]) * R(1.0 / 3.0) +
+                  (s_rho[hy + 1][hx + 1] + s_rho[hy + 1][hx - 1] - s_rho[hy - 1][hx - 1] - s_rho[hy - 1][hx + 1]) * R(1.0 / 12.0);
+    div_lam_gradT = rcv * R(P.chi) * lapT + R(P.cV) * R(P.chi) * (grx * gTx + gry * gTy);
+  }
+  const long long i = (long long)gy * P.nx + gx;
+  const R phi = div_lam_gradT * inv_rcv - R(P.kdiff) * lapT + T * (R(1) - dpdT * inv_rcv) * divv;
+  R S0 = phi;
+  if (P.model == 0) {
+    const R pp = first ? phi : phi_prev[i];
+    S0 = phi + R(0.5) * (phi - pp);
+  }
+  phi_prev[i] = phi;
+  collide_flow(f, rho, vx, vy, Fx, Fy, Q, P);
+  collide_heat(g, T, vx, vy, S0, P);
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    fdst[(long long)a * P.N + i] = (S)f[a];
+    gdst[(long long)a * P.N + i] = (S)g[a];
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+template <class S, class R, int TX, int TY>
+static cudaError_t fused_impl(const SplitBuffers& b, const DevParams& P, int cur, long long step, cudaStream_t st,
+                              cudaEvent_t* ev) {
+  dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
+  if (ev) cudaEventRecord(ev[0], st);
+  k_fused<S, R, TX, TY><<<grid, TX * TY, 0, st>>>((const S*)b.f[cur], (const S*)b.g[cur], (S*)b.f[cur ^ 1],
+                                                  (S*)b.g[cur ^ 1], (R*)b.phi_prev, P, step, step == 0, b.scalars,
+                                                  b.partials, b.status);
+  if (ev) cudaEventRecord(ev[1], st);
+  if (P.buoyancy) {
+    fused_finish(b, P, (int)(grid.x * grid.y), st);
+    if (ev) cudaEventRecord(ev[2], st);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t fused_step(const SplitBuffers& b, const DevParams& P, int prec, int cur, long long step, cudaStream_t st,
+                       cudaEvent_t* ev) {
+  return prec == 0 ? fused_impl<double, double, 32, 8>(b, P, cur, step, st, ev)
+                   : fused_impl<float, float, 32, 16>(b, P, cur, step, st, ev);
+}
+
+}  // namespace lbpc

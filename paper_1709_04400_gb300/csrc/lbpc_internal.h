@@ -33,4 +33,10 @@ cudaError_t split_export_pops(const SplitBuffers& b, const DevParams& P, int pre
 int split_nplanes();
 int split_block();
 
+// Fused single-kernel step (lbpc_fused.cu); same buffers, no scratch planes touched.
+cudaError_t fused_step(const SplitBuffers& b, const DevParams& P, int prec, int cur, long long step, cudaStream_t st,
+                       cudaEvent_t* ev = nullptr);
+// rho_ave <- sum of n per-tile partials / N (fixed order), on st.
+void fused_finish(const SplitBuffers& b, const DevParams& P, int n, cudaStream_t st);
+
 }  // namespace lbpc

@@ -375,6 +375,10 @@ cudaError_t split_export_pops(const SplitBuffers& b, const DevParams& P, int pre
   return cudaGetLastError();
 }
 
+void fused_finish(const SplitBuffers& b, const DevParams& P, int n, cudaStream_t st) {
+  k_finish<<<1, BLOCK, 0, st>>>(b.partials, n, 0, 1, 1.0 / (double)P.N, b.scalars);
+}
+
 int split_nplanes() { return NPLANES; }
 int split_block() { return BLOCK; }
 

@@ -24,11 +24,12 @@ PERIODIC, WALL, PRESSURE = 0, 1, 2
 T_NONE, T_DIRICHLET = 0, 1
 LAMBDA_CONST, LAMBDA_RHO_CV_CHI = 0, 1
 IMPROVED, COMPROMISED = 0, 1
+PATH_AUTO, PATH_SPLIT, PATH_FUSED = 0, 1, 2
 
 EXPORTED = ["lbpc_version", "lbpc_check_params", "lbpc_workspace_bytes", "lbpc_eos_critical", "lbpc_coexistence",
             "lbpc_create", "lbpc_init", "lbpc_step", "lbpc_step_async", "lbpc_check", "lbpc_fields", "lbpc_sums",
             "lbpc_populations", "lbpc_step_count", "lbpc_last_error", "lbpc_destroy", "lbpc_step_timed",
-            "lbpc_kernel_name"]
+            "lbpc_kernel_name", "lbpc_set_path"]
 
 
 class LbpcError(RuntimeError):
@@ -87,6 +88,7 @@ def load_library(path: str = LIB_PATH):
         "lbpc_step_timed": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
                                            ctypes.POINTER(ctypes.c_int32)]),
         "lbpc_kernel_name": (ctypes.c_char_p, [vp, ctypes.c_int32]),
+        "lbpc_set_path": (ctypes.c_int, [vp, ctypes.c_int32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -242,6 +244,10 @@ class Simulation:
             ptrs = [ctypes.c_void_p(0) if x is None else _ptr(x) for x in args]
             s = self.lib.lbpc_init(self.ctx, *ptrs, 0)
         self._raise(s, "lbpc_init")
+
+    def set_path(self, path):
+        """Kernel organisation of the step: PATH_AUTO, PATH_SPLIT or PATH_FUSED."""
+        self._raise(self.lib.lbpc_set_path(self.ctx, int(path)), "lbpc_set_path")
 
     def step(self, n=1, sync=True):
         s = (self.lib.lbpc_step if sync else self.lib.lbpc_step_async)(self.ctx, int(n))

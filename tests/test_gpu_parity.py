@@ -25,8 +25,13 @@ def _lib():
     torch.cuda.set_device(0)
 
 
-def _gpu(case, rho, T, steps, prec=lbpc.FP64):
+PATHS = [lbpc.PATH_SPLIT, lbpc.PATH_FUSED]
+PATH_IDS = ["split", "fused"]
+
+
+def _gpu(case, rho, T, steps, prec=lbpc.FP64, path=lbpc.PATH_AUTO):
     sim = lbpc.Simulation(lbpc.params_from_case(case, prec))
+    sim.set_path(path)
     sim.init(rho, T)
     sim.step(steps)
     out = sim.fields()
@@ -47,40 +52,44 @@ def _assert_within(err, tol):
     assert not bad, f"errors above {tol}: {err}"
 
 
-def test_mixed_boundaries_fp64():
+@pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
+def test_mixed_boundaries_fp64(path):
     """Wall + strip + pressure top + buoyancy + lambda = rho c_V chi + distinct thermal rates."""
     case, rho, T = workloads.mixed_small(TC, RV, RL)
     steps = 150
-    gpu, f, g, _ = _gpu(case, rho, T, steps)
+    gpu, f, g, _ = _gpu(case, rho, T, steps, path=path)
     p, s = run_oracle(case, rho, T, steps)
     _assert_within(_errors(gpu, p, s), 1e-10)
     assert np.max(np.abs(f - s.f)) / np.max(np.abs(s.f)) < 1e-10
     assert np.max(np.abs(g - s.g)) / np.max(np.abs(s.g)) < 1e-10
 
 
-def test_compromised_model_fp64():
+@pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
+def test_compromised_model_fp64(path):
     case, rho, T = workloads.mixed_small(TC, RV, RL, nx=33, ny=17)
     case = dict(case, model="compromised")
-    gpu, *_ = _gpu(case, rho, T, 100)
+    gpu, *_ = _gpu(case, rho, T, 100, path=path)
     p, s = run_oracle(case, rho, T, 100)
     _assert_within(_errors(gpu, p, s), 1e-10)
 
 
-def test_wall_top_and_pressure_bottom_fp64():
+@pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
+def test_wall_top_and_pressure_bottom_fp64(path):
     """The mirrored boundary set: wall on y+, pressure on y-, adiabatic (no Dirichlet) top."""
     case, rho, T = workloads.mixed_small(TC, RV, RL, nx=19, ny=23)
     rho = rho[::-1].copy()
     case = dict(case, flow_bc=("periodic", "periodic", "pressure", "wall"), rho_bc=(0, 0, RV, 0),
                 t_bc=("none", "none", "dirichlet", "none"), strip=None, gy=3e-5)
-    gpu, *_ = _gpu(case, rho, T, 100)
+    gpu, *_ = _gpu(case, rho, T, 100, path=path)
     p, s = run_oracle(case, rho, T, 100)
     _assert_within(_errors(gpu, p, s), 1e-10)
 
 
-def test_droplet_periodic_128_fp64_1000_steps():
+@pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
+def test_droplet_periodic_128_fp64_1000_steps(path):
     """The 128 x 128 periodic droplet: 1000 steps, 1e-10 on rho, u, T (spec parity bar)."""
     case, rho, T = workloads.droplet_periodic(TC, RV, RL)
-    gpu, _, _, (mass, heat) = _gpu(case, rho, T, 1000)
+    gpu, _, _, (mass, heat) = _gpu(case, rho, T, 1000, path=path)
     p, s = run_oracle(case, rho, T, 1000)
     err = _errors(gpu, p, s)
     _assert_within(err, 1e-10)
@@ -88,20 +97,22 @@ def test_droplet_periodic_128_fp64_1000_steps():
     assert abs(heat - s.g.sum()) / s.g.sum() < 1e-12
 
 
+@pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
 @pytest.mark.parametrize("dT", [0.05, 0.1, 0.2])
-def test_droplet_evaporation_256_fp64(dT):
+def test_droplet_evaporation_256_fp64(dT, path):
     """The 256 x 256 evaporation case at full size, 200 steps (the oracle's share of the run)."""
     case, rho, T = workloads.droplet_evaporation(TC, RV, RL, dT_ratio=dT)
-    gpu, *_ = _gpu(case, rho, T, 200)
+    gpu, *_ = _gpu(case, rho, T, 200, path=path)
     p, s = run_oracle(case, rho, T, 200)
     _assert_within(_errors(gpu, p, s), 1e-10)
 
 
-def test_heated_wall_fp32():
+@pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
+def test_heated_wall_fp32(path):
     """The 300 x 400 heated-wall pool in FP32 storage and arithmetic against the FP64 oracle."""
     case, rho, T = workloads.heated_wall(TC, RV, RL)
     steps = 100
-    gpu, *_ = _gpu(case, rho, T, steps, prec=lbpc.FP32)
+    gpu, *_ = _gpu(case, rho, T, steps, prec=lbpc.FP32, path=path)
     p, s = run_oracle(case, rho, T, steps)
     _assert_within(_errors(gpu, p, s), 1e-4)
 
@@ -185,3 +196,13 @@ def test_failure_matches_oracle():
     sim.close()
     assert eg.value.status == lbpc.LBPC_ENONPHYS
     assert f"step {eo.value.step}, node (x={eo.value.x}, y={eo.value.y})" in str(eg.value)
+
+
+@pytest.mark.parametrize("prec,tol", [(lbpc.FP64, 1e-12), (lbpc.FP32, 2e-5)], ids=["fp64", "fp32"])
+def test_split_and_fused_agree(prec, tol):
+    """The two kernel organisations compute the same step (they differ only in operation order)."""
+    case, rho, T = workloads.mixed_small(TC, RV, RL, nx=67, ny=45)
+    a, fa, ga, _ = _gpu(case, rho, T, 50, prec=prec, path=lbpc.PATH_SPLIT)
+    b, fb, gb, _ = _gpu(case, rho, T, 50, prec=prec, path=lbpc.PATH_FUSED)
+    assert np.max(np.abs(fa - fb)) / np.max(np.abs(fa)) < tol
+    assert np.max(np.abs(ga - gb)) / np.max(np.abs(ga)) < tol
