@@ -173,6 +173,44 @@ const char* lbpc_last_error(const lbpc_ctx* c);
 /* Free the context (not the workspace, not the stream). NULL is allowed. */
 void lbpc_destroy(lbpc_ctx* c);
 
+/* ------------------------------------------------------------------------------------------------
+ * One time step without any device allocation.
+ *
+ * Some callers cannot allocate device memory at all: an application whose device memory is handed
+ * out only by its own pool allocator, code that runs where cudaMalloc is not permitted, or a host
+ * program with no allocator of its own. lbpc_create needs a caller-allocated workspace that holds
+ * scratch planes besides the state. lbpc_step_static instead takes only the state (inputs and outputs)
+ * from the caller and keeps its scratch in a fixed static device array of the library. That array
+ * is sized for at most LBPC_STATIC_MAX_NODES nodes (256 x 256), about 6 MiB, and every GPU that loads
+ * the library holds it until the process exits. The paper has no counterpart; this is plumbing.
+ *
+ * It runs the same kernels as lbpc_step and lbpc_step_async, with the split organisation.
+ *
+ *   p         parameters, as for lbpc_create; nx * ny must not exceed LBPC_STATIC_MAX_NODES
+ *             (LBPC_ENOMEM otherwise, before any device work)
+ *   f_in,g_in post-collision populations of the previous step, device, [9][ny][nx] of the storage type
+ *             (lbpc_params.prec), D2Q9 order as for lbpc_populations; slot a of node x holds the value
+ *             that node x + e_a receives when it streams. A context's state has this form.
+ *   f_out,g_out  device buffers of the same size for the new post-collision populations; they must
+ *             not alias the inputs
+ *   phi_prev  device [ny][nx] of the arithmetic type: phi of the previous step in, this step's out
+ *             (ignored on input when step == 0)
+ *   rho_ave   device pointer to one double: the previous step's domain mean of rho in, this step's
+ *             out; used and updated only with buoyancy (may be NULL without it)
+ *   step      index of this step (0 = first step after the equilibrium start)
+ *   stream    cudaStream_t the work runs on; the call synchronises it before returning
+ * Returns LBPC_OK, LBPC_ENONPHYS if a node left the EOS range, LBPC_EINVAL, LBPC_ENOMEM or
+ * LBPC_ECUDA.
+ *
+ * The call allocates nothing: no cudaMalloc, no cudaFree, no allocating library routine. The first
+ * call on a device looks up the device address of the static array, with that device current; make
+ * that first call before any stream capture. Every call shares the one array, which keeps the last
+ * call's contents (the status word is cleared at the start of each call); calls that overlap on the
+ * GPU, from several threads or streams, race on it. */
+#define LBPC_STATIC_MAX_NODES (256 * 256)
+lbpc_status lbpc_step_static(const lbpc_params* p, const void* f_in, const void* g_in, void* f_out, void* g_out,
+                             void* phi_prev, double* rho_ave, int64_t step, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

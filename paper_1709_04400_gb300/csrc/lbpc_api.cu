@@ -193,6 +193,10 @@ template <class F> double bisect(F fn, double lo, double hi) {
 
 }  // namespace
 
+namespace lbpc {
+DevParams make_dev_params_public(const lbpc_params* p) { return make_dev_params(p); }
+}  // namespace lbpc
+
 // ================================================================================================
 // exported
 // ================================================================================================

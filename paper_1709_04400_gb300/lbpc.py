@@ -29,7 +29,7 @@ PATH_AUTO, PATH_SPLIT, PATH_FUSED = 0, 1, 2
 EXPORTED = ["lbpc_version", "lbpc_check_params", "lbpc_workspace_bytes", "lbpc_eos_critical", "lbpc_coexistence",
             "lbpc_create", "lbpc_init", "lbpc_step", "lbpc_step_async", "lbpc_check", "lbpc_fields", "lbpc_sums",
             "lbpc_populations", "lbpc_step_count", "lbpc_last_error", "lbpc_destroy", "lbpc_step_timed",
-            "lbpc_kernel_name", "lbpc_set_path"]
+            "lbpc_kernel_name", "lbpc_set_path", "lbpc_step_static"]
 
 
 class LbpcError(RuntimeError):
@@ -89,6 +89,7 @@ def load_library(path: str = LIB_PATH):
                                            ctypes.POINTER(ctypes.c_int32)]),
         "lbpc_kernel_name": (ctypes.c_char_p, [vp, ctypes.c_int32]),
         "lbpc_set_path": (ctypes.c_int, [vp, ctypes.c_int32]),
+        "lbpc_step_static": (ctypes.c_int, [P, vp, vp, vp, vp, vp, vp, ctypes.c_int64, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
