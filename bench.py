@@ -158,10 +158,12 @@ def collide_bytes_per_node(prec_bytes):
     return prec_bytes * (18 + 18 + 2 + 9)
 
 
-# Algorithmic FP64 operations of the collide kernel per node (each add, subtract, multiply, divide and
-# square root counted once; an FMA counts as its multiply and its add). Counted from the kernel
-# source, term by term; see the design notes for the breakdown.
-COLLIDE_FLOPS = {"const": 345, "rho_cv_chi": 366}
+# Algorithmic FP64 operations of the split collide kernel per node (each add, subtract, multiply and
+# divide counted once; an FMA counts as its multiply and its add), counted term by term from the
+# kernel: gradients 41, source 15, flow collision 140, thermal collision 64 with unit thermal rates
+# (116 otherwise); lambda = rho c_V chi adds 20 for grad rho.
+def collide_flops(lambda_mode, unit_heat_rates):
+    return 259 + (20 if lambda_mode == "rho_cv_chi" else 0) + (0 if unit_heat_rates else 52)
 
 
 def run_native(args):
@@ -238,12 +240,13 @@ def run_native(args):
     peak_bw = float(peaks.get("hbm_gbs", 6800.0))
     bw_src = "MEASURED_PEAKS.json hbm_gbs (burst copy)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
     if prec == lbpc.FP64 and "k_collide" in avg:
-        flops = COLLIDE_FLOPS[case["lambda_mode"]] * N
+        fpn = collide_flops(case["lambda_mode"], all(v == 1.0 for v in case["s_g"][1:]))
+        flops = fpn * N
         achieved = flops / (avg["k_collide"] / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": "k_collide", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
                 "frac": achieved / 1.25, "traffic": None,
                 "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s, profiling recipe); 1.20 measured FMA",
-                "flops_per_node": COLLIDE_FLOPS[case["lambda_mode"]], "top_kernel": top}
+                "flops_per_node": fpn, "top_kernel": top}
     elif "k_fused" in avg:
         bytes_ = fused_bytes_per_node(pb) * N
         achieved = bytes_ / (avg["k_fused"] / 1e3) / 1e9

@@ -110,6 +110,37 @@ bool is_dirichlet_ok(int v) { return v == LBPC_T_NONE || v == LBPC_T_DIRICHLET; 
 double critical_T(const lbpc_params* p) { return 0.0778 * p->a / (0.45724 * p->b * p->R); }
 double kappa_of(double om) { return 0.37464 + 1.54226 * om - 0.26992 * om * om; }
 
+template <class R> void fill_coefs(lbpc::Coefs<R>& c, const lbpc_params* p) {
+  for (int k = 0; k < 4; ++k) c.T_bc[k] = (R)p->T_bc[k];
+  c.T_strip = (R)p->T_strip;
+  c.rho_bc_lo = (R)p->rho_bc[2];
+  c.rho_bc_hi = (R)p->rho_bc[3];
+  c.a = (R)p->a;
+  c.b = (R)p->b;
+  c.R_gas = (R)p->R;
+  c.G = (R)p->G;
+  c.kappa = (R)kappa_of(p->omega);
+  for (int k = 0; k < 9; ++k) {
+    c.s_f[k] = (R)p->s_f[k];
+    c.s_g[k] = (R)p->s_g[k];
+    c.hf[k] = (R)(1.0 - 0.5 * p->s_f[k]);
+  }
+  c.lambda = (R)p->lambda;
+  c.chi = (R)p->chi;
+  c.cV = (R)p->cV;
+  c.kdiff = (R)((1.0 / p->s_g[3] - 0.5) / 3.0);
+  c.gx = (R)p->gx;
+  c.gy = (R)p->gy;
+  c.G_wall = (R)p->G_wall;
+  c.c3 = (R)((1.0 - 0.5 * p->s_g[3]) * p->s_g[4]);
+  c.c5 = (R)((1.0 - 0.5 * p->s_g[5]) * p->s_g[6]);
+  c.inv_Tc = (R)(1.0 / critical_T(p));
+  c.qG2 = (R)(12.0 * p->sigma / (1.0 / p->s_f[1] - 0.5) * p->G * p->G);
+  c.inv_cV = (R)(1.0 / p->cV);
+  c.psi_scale = (R)(2.0 / p->G);
+  c.cV_chi = (R)(p->cV * p->chi);
+}
+
 DevParams make_dev_params(const lbpc_params* p) {
   DevParams d{};
   d.nx = p->nx;
@@ -118,43 +149,16 @@ DevParams make_dev_params(const lbpc_params* p) {
   d.yper = p->flow_bc[2] == LBPC_PERIODIC;
   d.ybc_lo = p->flow_bc[2];
   d.ybc_hi = p->flow_bc[3];
-  for (int k = 0; k < 4; ++k) {
-    d.tbc[k] = p->t_bc[k];
-    d.T_bc[k] = p->T_bc[k];
-  }
+  for (int k = 0; k < 4; ++k) d.tbc[k] = p->t_bc[k];
   d.strip_x0 = p->strip_x0;
   d.strip_x1 = p->strip_x1;
-  d.T_strip = p->T_strip;
   d.model = p->model;
   d.lambda_mode = p->lambda_mode;
   d.buoyancy = p->buoyancy != 0;
-  d.rho_bc_lo = p->rho_bc[2];
-  d.rho_bc_hi = p->rho_bc[3];
-  d.a = p->a;
-  d.b = p->b;
-  d.R = p->R;
-  d.G = p->G;
-  d.Tc = critical_T(p);
-  d.kappa = kappa_of(p->omega);
-  for (int k = 0; k < 9; ++k) {
-    d.s_f[k] = p->s_f[k];
-    d.s_g[k] = p->s_g[k];
-  }
-  d.qcoef = 12.0 * p->sigma / (1.0 / p->s_f[1] - 0.5);
-  d.lambda = p->lambda;
-  d.chi = p->chi;
-  d.cV = p->cV;
-  d.kdiff = (1.0 / p->s_g[3] - 0.5) / 3.0;
-  d.gx = p->gx;
-  d.gy = p->gy;
-  d.G_wall = p->G_wall;
-  d.c3 = (1.0 - 0.5 * p->s_g[3]) * p->s_g[4];
-  d.c5 = (1.0 - 0.5 * p->s_g[5]) * p->s_g[6];
-  d.inv_Tc = 1.0 / d.Tc;
-  for (int k = 0; k < 9; ++k) d.hf[k] = 1.0 - 0.5 * p->s_f[k];
-  d.qG2 = d.qcoef * p->G * p->G;
-  d.inv_cV = 1.0 / p->cV;
-  d.psi_scale = 2.0 / p->G;
+  d.heat_unit_rates = 1;
+  for (int k = 1; k < 9; ++k) d.heat_unit_rates &= p->s_g[k] == 1.0;
+  fill_coefs(d.cd, p);
+  fill_coefs(d.cf, p);
   return d;
 }
 

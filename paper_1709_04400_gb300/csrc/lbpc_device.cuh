@@ -18,6 +18,24 @@ enum { ST_RHO_LE0 = 1, ST_RHO_POLE = 2, ST_T_LE0 = 3, ST_PSI2_NEG = 4, ST_NONFIN
 __host__ __device__ constexpr int EX(int a) { return a == 1 || a == 5 || a == 8 ? 1 : (a == 3 || a == 6 || a == 7 ? -1 : 0); }
 __host__ __device__ constexpr int EY(int a) { return a == 2 || a == 5 || a == 6 ? 1 : (a == 4 || a == 7 || a == 8 ? -1 : 0); }
 
+// Real-valued parameters in the arithmetic type of a kernel, folded on the host, so that a kernel
+// never converts between FP64 and FP32 (on GB300 those conversions run at the FP64 rate).
+template <class R> struct Coefs {
+  R T_bc[4], T_strip;
+  R rho_bc_lo, rho_bc_hi;
+  R a, b, R_gas, G, kappa;
+  R s_f[9], s_g[9];
+  R lambda, chi, cV, kdiff;  // kdiff = (1/s_g3 - 1/2) c_s^2
+  R gx, gy, G_wall;
+  R c3, c5;     // (1 - s3/2) s4, (1 - s5/2) s6 of Eqs. 54-55
+  R inv_Tc;     // 1 / T_c
+  R hf[9];      // 1 - s_f[k]/2, the forcing weights of (I - Lambda/2) S_F
+  R qG2;        // 12 sigma / (1/s_e - 1/2) * G^2: Q = qcoef |F_int|^2 / psi^2 = qG2 |sum_a w psi e|^2
+  R inv_cV;     // 1 / c_V
+  R psi_scale;  // 2 / G: psi^2 = (2/G) (p - rho c_s^2)
+  R cV_chi;     // c_V chi
+};
+
 // Everything a kernel needs, derived once on the host from lbpc_params and passed by value.
 struct DevParams {
   int nx, ny;
@@ -29,23 +47,14 @@ struct DevParams {
   int model;         // 0 improved, 1 compromised
   int lambda_mode;   // 0 const, 1 rho cV chi
   int buoyancy;
-  double T_bc[4], T_strip;
-  double rho_bc_lo, rho_bc_hi;
-  double a, b, R, G, Tc, kappa;
-  double s_f[9], s_g[9];
-  double qcoef;      // 12 sigma / (1/s_e - 1/2)
-  double lambda, chi, cV, kdiff;  // kdiff = (1/s_g3 - 1/2) c_s^2
-  double gx, gy, G_wall;
-  double c3, c5;     // (1 - s3/2) s4, (1 - s5/2) s6 of Eqs. 54-55
-  // constants folded on the host
-  double inv_Tc;     // 1 / T_c
-  double hf[9];      // 1 - s_f[k]/2, the forcing weights of (I - Lambda/2) S_F
-  double qG2;        // qcoef * G^2: Q = qcoef |F_int|^2 / psi^2 = qcoef G^2 |sum_a w psi e|^2
-  double inv_cV;     // 1 / c_V
-  double psi_scale;  // 2 / G: psi^2 = (2/G) (p - rho c_s^2)
+  int heat_unit_rates;  // s_g[1..8] all 1: the thermal relaxation sets every non-conserved moment to m_eq
+  Coefs<double> cd;
+  Coefs<float> cf;
 };
 
-template <class S> __device__ __forceinline__ double ld(const S* p) { return (double)__ldg(p); }
+template <class R> __host__ __device__ __forceinline__ const Coefs<R>& coefs(const DevParams& P);
+template <> __host__ __device__ __forceinline__ const Coefs<double>& coefs<double>(const DevParams& P) { return P.cd; }
+template <> __host__ __device__ __forceinline__ const Coefs<float>& coefs<float>(const DevParams& P) { return P.cf; }
 
 // ------------------------------------------------------------------------------------------------
 // moment transforms: m = M x and x = M^{-1} m with M^{-1} = M^T diag(1/9,1/36,1/36,1/6,1/12,1/6,1/12,1/4,1/4)
@@ -89,24 +98,33 @@ template <class R> __device__ __forceinline__ void from_moments(const R m[9], R 
 // ------------------------------------------------------------------------------------------------
 // Peng-Robinson EOS (Eq. 56) and (dp/dT)_rho
 // ------------------------------------------------------------------------------------------------
-template <class R> __device__ __forceinline__ void eos(R rho, R T, const DevParams& P, R& p, R& dpdT) {
+template <class R> __device__ __forceinline__ void eos(R rho, R T, const DevParams& P, R& p, R& dpdT, R* inv_rho = nullptr) {
+  const Coefs<R>& C = coefs<R>(P);
   // theta(T) = [1 + kappa (1 - sqrt(T/T_c))]^2 and d theta/dT = -kappa [..] / sqrt(T T_c); one rsqrt
   // gives both sqrt(T/T_c) = t rsqrt(t) and 1/sqrt(T T_c) = rsqrt(t) / T_c with t = T/T_c.
-  const R t = T * R(P.inv_Tc);
+  const R t = T * C.inv_Tc;
   const R rs = rsqrt(t);
   const R sq = t * rs;
-  const R th1 = R(1) + R(P.kappa) * (R(1) - sq);
+  const R th1 = R(1) + C.kappa * (R(1) - sq);
   const R theta = th1 * th1;
-  const R dtheta = -R(P.kappa) * th1 * rs * R(P.inv_Tc);
-  // 1/(1 - b rho) and 1/(1 + 2 b rho - b^2 rho^2) from one reciprocal of their product
-  const R br = R(P.b) * rho;
+  const R dtheta = -C.kappa * th1 * rs * C.inv_Tc;
+  // 1/(1 - b rho) and 1/(1 + 2 b rho - b^2 rho^2) (and 1/rho if asked) from one reciprocal
+  const R br = C.b * rho;
   const R d1 = R(1) - br;
   const R d2 = R(1) + R(2) * br - br * br;
-  const R r12 = R(1) / (d1 * d2);
+  const R d12 = d1 * d2;
+  R r12;
+  if (inv_rho) {
+    const R r = R(1) / (rho * d12);
+    *inv_rho = d12 * r;
+    r12 = rho * r;
+  } else {
+    r12 = R(1) / d12;
+  }
   const R inv1 = d2 * r12, inv2 = d1 * r12;
   const R r2 = rho * rho;
-  p = rho * R(P.R) * T * inv1 - R(P.a) * theta * r2 * inv2;
-  dpdT = rho * R(P.R) * inv1 - R(P.a) * dtheta * r2 * inv2;
+  p = rho * C.R_gas * T * inv1 - C.a * theta * r2 * inv2;
+  dpdT = rho * C.R_gas * inv1 - C.a * dtheta * r2 * inv2;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -128,13 +146,14 @@ __device__ __forceinline__ void pull(const S* __restrict__ src, const DevParams&
       v[a] = R(0);
       continue;
     }
-    v[a] = R(ld(src + (long long)a * P.N + (long long)sy * P.nx + sx));
+    v[a] = R(__ldg(src + (long long)a * P.N + (long long)sy * P.nx + sx));
   }
 }
 
 // Zou-He closure of the unknown f on a non-periodic y edge (wall: u = 0; pressure: rho = rho_bc, u_x = 0).
 template <class R> __device__ __forceinline__ void flow_closure(R f[9], const DevParams& P, int y) {
   if (P.yper) return;
+  const Coefs<R>& C = coefs<R>(P);
   const R d13 = f[1] - f[3];
   if (y == 0) {
     if (P.ybc_lo == BC_WALL) {
@@ -142,7 +161,7 @@ template <class R> __device__ __forceinline__ void flow_closure(R f[9], const De
       f[5] = f[7] - R(0.5) * d13;
       f[6] = f[8] + R(0.5) * d13;
     } else {
-      const R ru = R(P.rho_bc_lo) - (f[0] + f[1] + f[3] + R(2) * (f[4] + f[7] + f[8]));  // rho_bc u_y
+      const R ru = C.rho_bc_lo - (f[0] + f[1] + f[3] + R(2) * (f[4] + f[7] + f[8]));  // rho_bc u_y
       f[2] = f[4] + R(2.0 / 3.0) * ru;
       f[5] = f[7] - R(0.5) * d13 + ru * R(1.0 / 6.0);
       f[6] = f[8] + R(0.5) * d13 + ru * R(1.0 / 6.0);
@@ -153,7 +172,7 @@ template <class R> __device__ __forceinline__ void flow_closure(R f[9], const De
       f[7] = f[5] + R(0.5) * d13;
       f[8] = f[6] - R(0.5) * d13;
     } else {
-      const R ru = (f[0] + f[1] + f[3] + R(2) * (f[2] + f[5] + f[6])) - R(P.rho_bc_hi);  // rho_bc u_y
+      const R ru = (f[0] + f[1] + f[3] + R(2) * (f[2] + f[5] + f[6])) - C.rho_bc_hi;  // rho_bc u_y
       f[4] = f[2] - R(2.0 / 3.0) * ru;
       f[7] = f[5] + R(0.5) * d13 - ru * R(1.0 / 6.0);
       f[8] = f[6] - R(0.5) * d13 - ru * R(1.0 / 6.0);
@@ -179,12 +198,13 @@ template <class R> __device__ __forceinline__ void heat_meq(R T, R vx, R vy, int
 // the wall), g_a = g_opp(a) otherwise (zero heat flux). A Dirichlet edge of a periodic axis (a ring
 // inside a periodic domain) resets the node to g := M^{-1} m_eq(T_bc, 0): x edges, then y edges.
 template <class R> __device__ __forceinline__ void heat_closure(R g[9], const DevParams& P, int x, int y) {
+  const Coefs<R>& C = coefs<R>(P);
   if (!P.yper) {
     if (y == 0) {
       if (P.tbc[2]) {
-        const double Tb = (x >= P.strip_x0 && x < P.strip_x1) ? P.T_strip : P.T_bc[2];
+        const R Tb = (x >= P.strip_x0 && x < P.strip_x1) ? C.T_strip : C.T_bc[2];
         R n[9], e[9];
-        heat_meq(R(Tb), R(0), R(0), P.model, n);
+        heat_meq(Tb, R(0), R(0), P.model, n);
         from_moments(n, e);
         g[2] = R(2) * e[2] - g[4];
         g[5] = R(2) * e[5] - g[7];
@@ -196,7 +216,7 @@ template <class R> __device__ __forceinline__ void heat_closure(R g[9], const De
     if (y == P.ny - 1) {
       if (P.tbc[3]) {
         R n[9], e[9];
-        heat_meq(R(P.T_bc[3]), R(0), R(0), P.model, n);
+        heat_meq(C.T_bc[3], R(0), R(0), P.model, n);
         from_moments(n, e);
         g[4] = R(2) * e[4] - g[2];
         g[7] = R(2) * e[7] - g[5];
@@ -207,16 +227,16 @@ template <class R> __device__ __forceinline__ void heat_closure(R g[9], const De
     }
   }
   bool set = false;
-  double Tb = 0.0;
-  if (x == 0 && P.tbc[0]) { set = true; Tb = P.T_bc[0]; }
-  if (x == P.nx - 1 && P.tbc[1]) { set = true; Tb = P.T_bc[1]; }
+  R Tb = R(0);
+  if (x == 0 && P.tbc[0]) { set = true; Tb = C.T_bc[0]; }
+  if (x == P.nx - 1 && P.tbc[1]) { set = true; Tb = C.T_bc[1]; }
   if (P.yper) {
-    if (y == 0 && P.tbc[2]) { set = true; Tb = (x >= P.strip_x0 && x < P.strip_x1) ? P.T_strip : P.T_bc[2]; }
-    if (y == P.ny - 1 && P.tbc[3]) { set = true; Tb = P.T_bc[3]; }
+    if (y == 0 && P.tbc[2]) { set = true; Tb = (x >= P.strip_x0 && x < P.strip_x1) ? C.T_strip : C.T_bc[2]; }
+    if (y == P.ny - 1 && P.tbc[3]) { set = true; Tb = C.T_bc[3]; }
   }
   if (set) {
     R n[9];
-    heat_meq(R(Tb), R(0), R(0), P.model, n);
+    heat_meq(Tb, R(0), R(0), P.model, n);
     from_moments(n, g);
   }
 }
@@ -238,6 +258,7 @@ __device__ __forceinline__ void pull_closed(const S* __restrict__ fsrc, const S*
 // m* = m - Lambda (m - m_eq) + (I - Lambda/2) S_F, S_F with the sigma term Q in the energy moments.
 template <class R>
 __device__ __forceinline__ void collide_flow(R f[9], R rho, R vx, R vy, R Fx, R Fy, R Q, const DevParams& P) {
+  const Coefs<R>& C = coefs<R>(P);
   R m[9];
   to_moments(f, m);
   const R vxx = vx * vx, vyy = vy * vy;
@@ -256,7 +277,7 @@ __device__ __forceinline__ void collide_flow(R f[9], R rho, R vx, R vy, R Fx, R 
 #pragma unroll
   for (int k = 1; k < 9; ++k) {
     if (k == 3 || k == 5) continue;
-    m[k] = m[k] - R(P.s_f[k]) * (m[k] - meq[k]) + R(P.hf[k]) * SF[k];
+    m[k] = m[k] - C.s_f[k] * (m[k] - meq[k]) + C.hf[k] * SF[k];
   }
   from_moments(m, f);
 }
@@ -264,16 +285,32 @@ __device__ __forceinline__ void collide_flow(R f[9], R rho, R vx, R vy, R Fx, R 
 // Thermal MRT collision of the improved model: Eq. 45 with m_eq of Eq. 53 and S = (S0, 0, ..., 0)
 // (Eq. 46), then m3* += (1 - s3/2) s4 (m4 - m4_eq) and m5* += (1 - s5/2) s6 (m6 - m6_eq) (Eqs. 54-55).
 template <class R> __device__ __forceinline__ void collide_heat(R g[9], R T, R vx, R vy, R S0, const DevParams& P) {
-  R n[9], neq[9];
-  to_moments(g, n);
-  heat_meq(T, vx, vy, P.model, neq);
+  const Coefs<R>& C = coefs<R>(P);
   R ns[9];
-  ns[0] = n[0] + S0;  // n0_eq = T = n0: the relaxation leaves the zeroth moment, the source adds S0
+  if (P.heat_unit_rates) {
+    // s_k = 1 for k >= 1: every non-conserved moment relaxes to its equilibrium, so only the zeroth
+    // moment (T) and, for Eqs. 54-55, m4 and m6 of g are needed.
+    heat_meq(T, vx, vy, P.model, ns);
+    ns[0] = T + S0;
+    if (P.model == 0) {
+      const R n4 = R(-2) * (g[1] - g[3]) + (g[5] - g[6] - g[7] + g[8]);
+      const R n6 = R(-2) * (g[2] - g[4]) + (g[5] + g[6] - g[7] - g[8]);
+      ns[3] += C.c3 * (n4 - ns[4]);
+      ns[5] += C.c5 * (n6 - ns[6]);
+    }
+    ns[7] = R(0);
+    ns[8] = R(0);
+  } else {
+    R n[9], neq[9];
+    to_moments(g, n);
+    heat_meq(T, vx, vy, P.model, neq);
+    ns[0] = n[0] + S0;  // n0_eq = T = n0: the relaxation leaves the zeroth moment, the source adds S0
 #pragma unroll
-  for (int k = 1; k < 9; ++k) ns[k] = n[k] - R(P.s_g[k]) * (n[k] - neq[k]);
-  if (P.model == 0) {
-    ns[3] += R(P.c3) * (n[4] - neq[4]);
-    ns[5] += R(P.c5) * (n[6] - neq[6]);
+    for (int k = 1; k < 9; ++k) ns[k] = n[k] - C.s_g[k] * (n[k] - neq[k]);
+    if (P.model == 0) {
+      ns[3] += C.c3 * (n[4] - neq[4]);
+      ns[5] += C.c5 * (n[6] - neq[6]);
+    }
   }
   from_moments(ns, g);
 }
@@ -310,7 +347,7 @@ __device__ __forceinline__ void report(long long* status, long long step, int x,
 template <class R> __device__ __forceinline__ int classify(R rho, R T, R psi2, const DevParams& P) {
   if (!isfinite(rho) || !isfinite(T) || !isfinite(psi2)) return ST_NONFINITE;
   if (!(rho > R(0))) return ST_RHO_LE0;
-  if (!(R(P.b) * rho < R(1))) return ST_RHO_POLE;
+  if (!(coefs<R>(P).b * rho < R(1))) return ST_RHO_POLE;
   if (!(T > R(0))) return ST_T_LE0;
   if (!(psi2 >= R(0))) return ST_PSI2_NEG;
   return 0;

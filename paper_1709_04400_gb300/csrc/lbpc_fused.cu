@@ -19,8 +19,16 @@ namespace lbpc {
 namespace {
 
 __device__ __forceinline__ int wrap_any(int x, int n) {
-  x %= n;
-  return x < 0 ? x + n : x;
+  while (x < 0) x += n;  // at most a few iterations: x stays within a few tiles of [0, n)
+  while (x >= n) x -= n;
+  return x;
+}
+
+// Post-stream populations of an interior node (no wrap, no closure): src[a][i - e_a].
+template <class S, class R>
+__device__ __forceinline__ void pull_interior(const S* __restrict__ src, long long N, int nx, long long i, R v[9]) {
+#pragma unroll
+  for (int a = 0; a < 9; ++a) v[a] = R(__ldg(src + (long long)a * N + i - (long long)EY(a) * nx - EX(a)));
 }
 
 // Domain row for region row offset: wraps when y is periodic, else clamps to the edge row.
@@ -31,19 +39,34 @@ __device__ __forceinline__ int row_of(const DevParams& P, int y) {
 
 }  // namespace
 
-template <class S, class R, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY) k_fused(const S* __restrict__ fsrc, const S* __restrict__ gsrc,
-                                                   S* __restrict__ fdst, S* __restrict__ gdst,
-                                                   R* __restrict__ phi_prev, DevParams P, long long step, int first,
-                                                   const double* __restrict__ rho_ave, double* __restrict__ partials,
-                                                   long long* __restrict__ status) {
+template <class R, int TX, int TY> struct FusedSmem {
+  R rho[TY + 4][TX + 4], T[TY + 4][TX + 4], psi[TY + 4][TX + 4], jx[TY + 4][TX + 4], jy[TY + 4][TX + 4];
+  R vx[TY + 2][TX + 2], vy[TY + 2][TX + 2];
+  double red[TX * TY / 32];
+};
+
+// INTERIOR: the tile, its 2-ring and their pull sources lie inside the domain away from every edge,
+// so no index wraps, no boundary closure applies and no ghost row exists (a per-CTA, uniform choice).
+template <bool INTERIOR, class S, class R, int TX, int TY>
+__device__ __forceinline__ void fused_body(const S* __restrict__ fsrc, const S* __restrict__ gsrc,
+                                           S* __restrict__ fdst, S* __restrict__ gdst, R* __restrict__ phi_prev,
+                                           const DevParams& P, long long step, int first,
+                                           const double* __restrict__ rho_ave, double* __restrict__ partials,
+                                           long long* __restrict__ status, FusedSmem<R, TX, TY>& sm) {
   constexpr int RX = TX + 4, RY = TY + 4;  // stage-1 region (tile + 2)
   constexpr int VX = TX + 2, VY = TY + 2;  // stage-2 region (tile + 1)
+  (void)RY;
   constexpr int NT = TX * TY;
-  __shared__ R s_rho[RY][RX], s_T[RY][RX], s_psi[RY][RX], s_jx[RY][RX], s_jy[RY][RX];
-  __shared__ R s_vx[VY][VX], s_vy[VY][VX];
-  __shared__ double s_red[NT / 32];
+  auto& s_rho = sm.rho;
+  auto& s_T = sm.T;
+  auto& s_psi = sm.psi;
+  auto& s_jx = sm.jx;
+  auto& s_jy = sm.jy;
+  auto& s_vx = sm.vx;
+  auto& s_vy = sm.vy;
+  double* s_red = sm.red;
 
+  const Coefs<R>& C = coefs<R>(P);
   const int t = threadIdx.x;
   const int tx = t % TX, ty = t / TX;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -53,7 +76,13 @@ __global__ void __launch_bounds__(TX* TY) k_fused(const S* __restrict__ fsrc, co
 
   // ---- stage 1a: own node (kept in registers) ----
   R f[9], g[9];
-  pull_closed<S, R>(fsrc, gsrc, P, mx, my, f, g);
+  if (INTERIOR) {
+    const long long io = (long long)gy * P.nx + gx;
+    pull_interior<S, R>(fsrc, P.N, P.nx, io, f);
+    pull_interior<S, R>(gsrc, P.N, P.nx, io, g);
+  } else {
+    pull_closed<S, R>(fsrc, gsrc, P, mx, my, f, g);
+  }
   R rho, T, p, dpdT;
   {
     rho = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
@@ -61,7 +90,7 @@ __global__ void __launch_bounds__(TX* TY) k_fused(const S* __restrict__ fsrc, co
     const R jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
     T = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
     eos(rho, T, P, p, dpdT);
-    const R psi2 = R(P.psi_scale) * (p - rho * R(1.0 / 3.0));
+    const R psi2 = C.psi_scale * (p - rho * R(1.0 / 3.0));
     if (active) {
       const int bad = classify(rho, T, psi2, P);
       if (bad) report(status, step, gx, gy, bad);
@@ -86,14 +115,20 @@ __global__ void __launch_bounds__(TX* TY) k_fused(const S* __restrict__ fsrc, co
       const int c = q % 4;
       hx = c < 2 ? c : TX + c;
     }
-    const int x = wrap_any(x0 + hx - 2, P.nx), y = row_of(P, y0 + hy - 2);
     R fr[9], gr[9];
-    pull_closed<S, R>(fsrc, gsrc, P, x, y, fr, gr);
+    if (INTERIOR) {
+      const long long io = (long long)(y0 + hy - 2) * P.nx + (x0 + hx - 2);
+      pull_interior<S, R>(fsrc, P.N, P.nx, io, fr);
+      pull_interior<S, R>(gsrc, P.N, P.nx, io, gr);
+    } else {
+      const int x = wrap_any(x0 + hx - 2, P.nx), y = row_of(P, y0 + hy - 2);
+      pull_closed<S, R>(fsrc, gsrc, P, x, y, fr, gr);
+    }
     const R rr = fr[0] + fr[1] + fr[2] + fr[3] + fr[4] + fr[5] + fr[6] + fr[7] + fr[8];
     const R Tr = gr[0] + gr[1] + gr[2] + gr[3] + gr[4] + gr[5] + gr[6] + gr[7] + gr[8];
     R pr, dr;
     eos(rr, Tr, P, pr, dr);
-    const R psi2 = R(P.psi_scale) * (pr - rr * R(1.0 / 3.0));
+    const R psi2 = C.psi_scale * (pr - rr * R(1.0 / 3.0));
     s_rho[hy][hx] = rr;
     s_T[hy][hx] = Tr;
     s_psi[hy][hx] = sqrt(fmax(psi2, R(0)));
@@ -119,26 +154,26 @@ __global__ void __launch_bounds__(TX* TY) k_fused(const S* __restrict__ fsrc, co
     const R pc = s_psi[hy][hx];
     const R sx = (c12 - c10) * R(1.0 / 3.0) + (c22 - c20 - c00 + c02) * R(1.0 / 12.0);
     const R sy = (c21 - c01) * R(1.0 / 3.0) + (c22 + c20 - c00 - c02) * R(1.0 / 12.0);
-    Fx = -R(P.G) * pc * sx;
-    Fy = -R(P.G) * pc * sy;
-    if (!P.yper) {
-      if (y == 0 && P.ybc_lo == BC_WALL) Fy += R(0.5) * R(P.G_wall) * pc;
-      if (y == P.ny - 1 && P.ybc_hi == BC_WALL) Fy -= R(0.5) * R(P.G_wall) * pc;
+    Fx = -C.G * pc * sx;
+    Fy = -C.G * pc * sy;
+    if (!INTERIOR && !P.yper) {
+      if (y == 0 && P.ybc_lo == BC_WALL) Fy += R(0.5) * C.G_wall * pc;
+      if (y == P.ny - 1 && P.ybc_hi == BC_WALL) Fy -= R(0.5) * C.G_wall * pc;
     }
     const R rr = s_rho[hy][hx];
     if (P.buoyancy) {
       const R d = rr - rho_ref;
-      Fx += d * R(P.gx);
-      Fy += d * R(P.gy);
+      Fx += d * C.gx;
+      Fy += d * C.gy;
     }
-    Q = R(P.qG2) * (sx * sx + sy * sy);
+    Q = C.qG2 * (sx * sx + sy * sy);
     const R ir = R(1) / rr;
     vx = (s_jx[hy][hx] + R(0.5) * Fx) * ir;
     vy = (s_jy[hy][hx] + R(0.5) * Fy) * ir;
   };
   // region row (stage-1 coordinates) holding the clamped domain row of stage-1 row hy
   auto clamp_hy = [&](int hy) {
-    if (P.yper) return hy;
+    if (INTERIOR || P.yper) return hy;
     const int y = y0 + hy - 2;
     if (y < 0) return hy - y;                 // row of y = 0
     if (y >= P.ny) return hy - (y - (P.ny - 1));  // row of y = ny - 1
@@ -187,20 +222,20 @@ __global__ void __launch_bounds__(TX* TY) k_fused(const S* __restrict__ fsrc, co
                  (s_vx[uy + 1][ux + 1] - s_vx[uy + 1][ux - 1] - s_vx[uy - 1][ux - 1] + s_vx[uy - 1][ux + 1]) * R(1.0 / 12.0) +
                  (s_vy[uy + 1][ux] - s_vy[uy - 1][ux]) * R(1.0 / 3.0) +
                  (s_vy[uy + 1][ux + 1] + s_vy[uy + 1][ux - 1] - s_vy[uy - 1][ux - 1] - s_vy[uy - 1][ux + 1]) * R(1.0 / 12.0);
-  const R rcv = rho * R(P.cV);
+  const R rcv = rho * C.cV;
   const R inv_rcv = R(1) / rcv;
   R div_lam_gradT;
   if (P.lambda_mode == 0) {
-    div_lam_gradT = R(P.lambda) * lapT;
+    div_lam_gradT = C.lambda * lapT;
   } else {
     const R grx = (s_rho[hy][hx + 1] - s_rho[hy][hx - 1]) * R(1.0 / 3.0) +
                   (s_rho[hy + 1][hx + 1] - s_rho[hy + 1][hx - 1] - s_rho[hy - 1][hx - 1] + s_rho[hy - 1][hx + 1]) * R(1.0 / 12.0);
     const R gry = (s_rho[hy + 1][hx] - s_rho[hy - 1][hx]) * R(1.0 / 3.0) +
                   (s_rho[hy + 1][hx + 1] + s_rho[hy + 1][hx - 1] - s_rho[hy - 1][hx - 1] - s_rho[hy - 1][hx + 1]) * R(1.0 / 12.0);
-    div_lam_gradT = rcv * R(P.chi) * lapT + R(P.cV) * R(P.chi) * (grx * gTx + gry * gTy);
+    div_lam_gradT = rcv * C.chi * lapT + C.cV_chi * (grx * gTx + gry * gTy);
   }
   const long long i = (long long)gy * P.nx + gx;
-  const R phi = div_lam_gradT * inv_rcv - R(P.kdiff) * lapT + T * (R(1) - dpdT * inv_rcv) * divv;
+  const R phi = div_lam_gradT * inv_rcv - C.kdiff * lapT + T * (R(1) - dpdT * inv_rcv) * divv;
   R S0 = phi;
   if (P.model == 0) {
     const R pp = first ? phi : phi_prev[i];
@@ -214,6 +249,21 @@ __global__ void __launch_bounds__(TX* TY) k_fused(const S* __restrict__ fsrc, co
     fdst[(long long)a * P.N + i] = (S)f[a];
     gdst[(long long)a * P.N + i] = (S)g[a];
   }
+}
+
+template <class S, class R, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY) k_fused(const S* __restrict__ fsrc, const S* __restrict__ gsrc,
+                                                   S* __restrict__ fdst, S* __restrict__ gdst,
+                                                   R* __restrict__ phi_prev, DevParams P, long long step, int first,
+                                                   const double* __restrict__ rho_ave, double* __restrict__ partials,
+                                                   long long* __restrict__ status) {
+  __shared__ FusedSmem<R, TX, TY> sm;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const bool interior = x0 >= 3 && x0 + TX + 3 <= P.nx && y0 >= 3 && y0 + TY + 3 <= P.ny;
+  if (interior)
+    fused_body<true, S, R, TX, TY>(fsrc, gsrc, fdst, gdst, phi_prev, P, step, first, rho_ave, partials, status, sm);
+  else
+    fused_body<false, S, R, TX, TY>(fsrc, gsrc, fdst, gdst, phi_prev, P, step, first, rho_ave, partials, status, sm);
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -69,6 +69,7 @@ __global__ void __launch_bounds__(BLOCK) k_macro(const S* __restrict__ fsrc, con
                                                  DevParams P, long long step, int do_partials,
                                                  double* __restrict__ partials, long long* __restrict__ status) {
   __shared__ double red[BLOCK / 32];
+  const Coefs<R>& C = coefs<R>(P);
   const long long i = (long long)blockIdx.x * BLOCK + threadIdx.x;
   double rho_d = 0.0;
   if (i < P.N) {
@@ -79,9 +80,9 @@ __global__ void __launch_bounds__(BLOCK) k_macro(const S* __restrict__ fsrc, con
     const R jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
     const R jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
     const R T = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
-    R p, dpdT;
-    eos(rho, T, P, p, dpdT);
-    const R psi2 = R(P.psi_scale) * (p - rho * R(1.0 / 3.0));
+    R p, dpdT, inv_rho;
+    eos(rho, T, P, p, dpdT, &inv_rho);
+    const R psi2 = C.psi_scale * (p - rho * R(1.0 / 3.0));
     const int bad = classify(rho, T, psi2, P);
     if (bad) report(status, step, x, y, bad);
     pl.p[P_RHO][i] = rho;
@@ -90,8 +91,8 @@ __global__ void __launch_bounds__(BLOCK) k_macro(const S* __restrict__ fsrc, con
     pl.p[P_JX][i] = jx;
     pl.p[P_JY][i] = jy;
     pl.p[P_DPDT][i] = dpdT;
-    pl.p[P_IRHO][i] = R(1) / rho;
-    rho_d = (double)rho;
+    pl.p[P_IRHO][i] = inv_rho;
+    if (do_partials) rho_d = (double)rho;
   }
   if (do_partials) {
     const double s = block_sum<BLOCK>(rho_d, red);
@@ -101,6 +102,7 @@ __global__ void __launch_bounds__(BLOCK) k_macro(const S* __restrict__ fsrc, con
 
 template <class R>
 __global__ void __launch_bounds__(BLOCK) k_force(Planes<R> pl, DevParams P, const double* __restrict__ rho_ave) {
+  const Coefs<R>& C = coefs<R>(P);
   const long long i = (long long)blockIdx.x * BLOCK + threadIdx.x;
   if (i >= P.N) return;
   const int y = (int)(i / P.nx), x = (int)(i - (long long)y * P.nx);
@@ -112,18 +114,18 @@ __global__ void __launch_bounds__(BLOCK) k_force(Planes<R> pl, DevParams P, cons
   const R pc = psi[i];
   const R sx = (c[1][2] - c[1][0]) * R(1.0 / 3.0) + (c[2][2] - c[2][0] - c[0][0] + c[0][2]) * R(1.0 / 12.0);
   const R sy = (c[2][1] - c[0][1]) * R(1.0 / 3.0) + (c[2][2] + c[2][0] - c[0][0] - c[0][2]) * R(1.0 / 12.0);
-  const R Fix = -R(P.G) * pc * sx, Fiy = -R(P.G) * pc * sy;
+  const R Fix = -C.G * pc * sx, Fiy = -C.G * pc * sy;
   R Fx = Fix, Fy = Fiy;
   // F_ads = -G_w psi(x) sum_a w_a s(x+e_a) e_a: the solid ghost row gives sum = (0, -1/2) below, (0, 1/2) above.
   if (!P.yper) {
-    if (y == 0 && P.ybc_lo == BC_WALL) Fy += R(0.5) * R(P.G_wall) * pc;
-    if (y == P.ny - 1 && P.ybc_hi == BC_WALL) Fy -= R(0.5) * R(P.G_wall) * pc;
+    if (y == 0 && P.ybc_lo == BC_WALL) Fy += R(0.5) * C.G_wall * pc;
+    if (y == P.ny - 1 && P.ybc_hi == BC_WALL) Fy -= R(0.5) * C.G_wall * pc;
   }
   const R rho = pl.p[P_RHO][i];
   if (P.buoyancy) {  // F_b = (rho - rho_ave) g (Sec. IV B)
     const R dr = rho - R(*rho_ave);
-    Fx += dr * R(P.gx);
-    Fy += dr * R(P.gy);
+    Fx += dr * C.gx;
+    Fy += dr * C.gy;
   }
   const R inv_rho = pl.p[P_IRHO][i];
   pl.p[P_VX][i] = (pl.p[P_JX][i] + R(0.5) * Fx) * inv_rho;
@@ -131,21 +133,37 @@ __global__ void __launch_bounds__(BLOCK) k_force(Planes<R> pl, DevParams P, cons
   pl.p[P_FX][i] = Fx;
   pl.p[P_FY][i] = Fy;
   // sigma term Q = qcoef |F_int|^2 / psi^2 = qcoef G^2 (sx^2 + sy^2): psi^2 cancels
-  pl.p[P_Q][i] = R(P.qG2) * (sx * sx + sy * sy);
+  pl.p[P_Q][i] = C.qG2 * (sx * sx + sy * sy);
 }
 
+// Two warp-uniform roles per node: the first BLOCK threads of a block run the flow collision of
+// BLOCK nodes, the next BLOCK threads run the source and thermal collision of the same nodes. The
+// roles share no data (both read the scratch planes), so a node's work splits into two independent
+// chains and twice as many warps hide the FP64 latency on small grids.
 template <class S, class R>
-__global__ void __launch_bounds__(BLOCK) k_collide(const S* __restrict__ fsrc, const S* __restrict__ gsrc,
-                                                   S* __restrict__ fdst, S* __restrict__ gdst, Planes<R> pl,
-                                                   R* __restrict__ phi_prev, DevParams P, int first) {
-  const long long i = (long long)blockIdx.x * BLOCK + threadIdx.x;
+__global__ void __launch_bounds__(2 * BLOCK) k_collide(const S* __restrict__ fsrc, const S* __restrict__ gsrc,
+                                                       S* __restrict__ fdst, S* __restrict__ gdst, Planes<R> pl,
+                                                       R* __restrict__ phi_prev, DevParams P, int first) {
+  const Coefs<R>& C = coefs<R>(P);
+  const bool heat = threadIdx.x >= BLOCK;
+  const long long i = (long long)blockIdx.x * BLOCK + (threadIdx.x - (heat ? BLOCK : 0));
   if (i >= P.N) return;
   const int y = (int)(i / P.nx), x = (int)(i - (long long)y * P.nx);
-  R f[9], g[9];
-  pull_closed<S, R>(fsrc, gsrc, P, x, y, f, g);
+  const R vx = pl.p[P_VX][i], vy = pl.p[P_VY][i];
+  if (!heat) {
+    R f[9];
+    pull<S, R>(fsrc, P, x, y, f);
+    flow_closure(f, P, y);
+    collide_flow(f, pl.p[P_RHO][i], vx, vy, pl.p[P_FX][i], pl.p[P_FY][i], pl.p[P_Q][i], P);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) fdst[(long long)a * P.N + i] = (S)f[a];
+    return;
+  }
+  R g[9];
+  pull<S, R>(gsrc, P, x, y, g);
+  heat_closure(g, P, x, y);
   const R rho = pl.p[P_RHO][i];
   const R T = pl.p[P_T][i];
-  const R vx = pl.p[P_VX][i], vy = pl.p[P_VY][i];
   // gradients feeding the source (isotropic differences)
   R c[3][3];
   gather9(pl.p[P_T], P, x, y, c);
@@ -154,30 +172,26 @@ __global__ void __launch_bounds__(BLOCK) k_collide(const S* __restrict__ fsrc, c
   R divv = d_x(c);
   gather9(pl.p[P_VY], P, x, y, c);
   divv += d_y(c);
-  const R rcv = rho * R(P.cV);
-  const R inv_rcv = pl.p[P_IRHO][i] * R(P.inv_cV);
+  const R rcv = rho * C.cV;
+  const R inv_rcv = pl.p[P_IRHO][i] * C.inv_cV;
   R div_lam_gradT;
   if (P.lambda_mode == 0) {
-    div_lam_gradT = R(P.lambda) * lapT;
+    div_lam_gradT = C.lambda * lapT;
   } else {  // lambda = rho c_V chi: lambda lap T + c_V chi grad rho . grad T
     gather9(pl.p[P_RHO], P, x, y, c);
-    div_lam_gradT = rcv * R(P.chi) * lapT + R(P.cV) * R(P.chi) * (d_x(c) * gTx + d_y(c) * gTy);
+    div_lam_gradT = rcv * C.chi * lapT + C.cV_chi * (d_x(c) * gTx + d_y(c) * gTy);
   }
   // phi: the underlined terms of Eq. 28 with k = (1/s_3 - 1/2) c_s^2
-  const R phi = div_lam_gradT * inv_rcv - R(P.kdiff) * lapT + T * (R(1) - pl.p[P_DPDT][i] * inv_rcv) * divv;
+  const R phi = div_lam_gradT * inv_rcv - C.kdiff * lapT + T * (R(1) - pl.p[P_DPDT][i] * inv_rcv) * divv;
   R S0 = phi;
   if (P.model == 0) {  // S0 = phi + 0.5 dt d_t phi, d_t phi ~ [phi(t) - phi(t - dt)]/dt (Eq. 46)
     const R pp = first ? phi : phi_prev[i];
     S0 = phi + R(0.5) * (phi - pp);
   }
   phi_prev[i] = phi;
-  collide_flow(f, rho, vx, vy, pl.p[P_FX][i], pl.p[P_FY][i], pl.p[P_Q][i], P);
   collide_heat(g, T, vx, vy, S0, P);
 #pragma unroll
-  for (int a = 0; a < 9; ++a) {
-    fdst[(long long)a * P.N + i] = (S)f[a];
-    gdst[(long long)a * P.N + i] = (S)g[a];
-  }
+  for (int a = 0; a < 9; ++a) gdst[(long long)a * P.N + i] = (S)g[a];
 }
 
 // Fixed-order sum of the block partials: each thread accumulates a strided subset in order, then one
@@ -299,7 +313,7 @@ static cudaError_t step_impl(const SplitBuffers& b, const DevParams& P, int cur,
   if (ev) cudaEventRecord(ev[1], st);
   k_force<R><<<nb, BLOCK, 0, st>>>(pl, P, b.scalars);
   if (ev) cudaEventRecord(ev[2], st);
-  k_collide<S, R><<<nb, BLOCK, 0, st>>>(fs, gs, (S*)b.f[cur ^ 1], (S*)b.g[cur ^ 1], pl, (R*)b.phi_prev, P, step == 0);
+  k_collide<S, R><<<nb, 2 * BLOCK, 0, st>>>(fs, gs, (S*)b.f[cur ^ 1], (S*)b.g[cur ^ 1], pl, (R*)b.phi_prev, P, step == 0);
   if (ev) cudaEventRecord(ev[3], st);
   if (P.buoyancy) {
     k_finish<<<1, BLOCK, 0, st>>>(b.partials, (int)nb, 0, 1, 1.0 / (double)P.N, b.scalars);
