@@ -38,7 +38,7 @@ def parse():
     ap.add_argument("--workload", default="evaporation", choices=["evaporation", "droplet", "heated_wall"])
     ap.add_argument("--n", type=int, default=0, help="grid side (0 = the workload's own size)")
     ap.add_argument("--dT", type=float, default=0.1, help="superheat dT / T_c of the evaporation case")
-    ap.add_argument("--prec", default="", choices=["", "fp64", "fp32"])
+    ap.add_argument("--prec", default="", choices=["", "fp64", "fp32", "fp16"])
     ap.add_argument("--path", default="auto", choices=["auto", "split", "fused"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -146,8 +146,11 @@ def cpu_baseline(case, rho, T, budget_s=12.0):
 
 
 # Algorithmic HBM traffic per node and step of the fused kernel: read 9 f + 9 g, write 9 f* + 9 g*,
-# read and write phi_prev (152 B in FP32, 304 B in FP64).
+# read and write phi_prev (304 B in FP64, 152 B in FP32); FP16 deviation storage moves 2-byte
+# populations plus the FP32 reference density and temperature (read and written) and FP32 phi: 96 B.
 def fused_bytes_per_node(prec_bytes):
+    if prec_bytes == 2:
+        return 2 * 36 + 4 * 4 + 4 * 2
     return prec_bytes * (18 + 18 + 2)
 
 
@@ -182,7 +185,7 @@ def run_native(args):
     Tc, _ = lbpc.eos_critical(p0)
     rv, rl, _ = lbpc.coexistence(p0, 0.86 * Tc)
     case, rho, T, prec_name = make_case(args, Tc, rv, rl)
-    prec = lbpc.FP64 if prec_name == "fp64" else lbpc.FP32
+    prec = {"fp64": lbpc.FP64, "fp32": lbpc.FP32, "fp16": lbpc.FP16DEV}[prec_name]
     params = lbpc.params_from_case(case, prec)
     N = case["nx"] * case["ny"]
 
@@ -236,7 +239,7 @@ def run_native(args):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    pb = 8 if prec == lbpc.FP64 else 4
+    pb = {lbpc.FP64: 8, lbpc.FP32: 4, lbpc.FP16DEV: 2}[prec]
     peak_bw = float(peaks.get("hbm_gbs", 6800.0))
     bw_src = "MEASURED_PEAKS.json hbm_gbs (burst copy)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
     if prec == lbpc.FP64 and "k_collide" in avg:

@@ -45,8 +45,12 @@ typedef enum {
   LBPC_ESTATE = 6     /* the context holds an earlier error */
 } lbpc_status;
 
-/* Storage precision of the populations f, g (arithmetic: FP64 for LBPC_FP64, FP32 otherwise). */
-typedef enum { LBPC_FP64 = 0, LBPC_FP32 = 1 } lbpc_prec;
+/* Storage precision of the populations f, g (arithmetic: FP64 for LBPC_FP64, FP32 otherwise).
+ * LBPC_FP16DEV stores each post-collision population as binary16 of its deviation from the rest-state
+ * equilibrium w_a * ref of the node that stored it, ref being that node's density (f) or
+ * post-collision temperature (g), kept in FP32 planes beside the populations: 2 bytes per population
+ * plus 4 per node and set, 96 B per node and step against 152 B for LBPC_FP32. */
+typedef enum { LBPC_FP64 = 0, LBPC_FP32 = 1, LBPC_FP16DEV = 2 } lbpc_prec;
 
 /* Flow boundary of an edge. x edges must be periodic; y edges are both periodic or both not.
  * A non-periodic y edge is an on-node row closed by the Zou-He scheme (the paper applies Zou-He at
@@ -144,7 +148,7 @@ const char* lbpc_kernel_name(const lbpc_ctx* c, int32_t k);
  * scratch planes (each EOS evaluated once per node; the faster choice when FP64 arithmetic bounds
  * the step). LBPC_PATH_FUSED: one kernel per step over shared-memory tiles (populations read once
  * and written once; the faster choice when HBM bounds the step). LBPC_PATH_AUTO (default): split
- * for LBPC_FP64, fused for LBPC_FP32. Both compute the same step. */
+ * for LBPC_FP64, fused for LBPC_FP32 and LBPC_FP16DEV. Both compute the same step. */
 typedef enum { LBPC_PATH_AUTO = 0, LBPC_PATH_SPLIT = 1, LBPC_PATH_FUSED = 2 } lbpc_path;
 lbpc_status lbpc_set_path(lbpc_ctx* c, int32_t path);
 
@@ -186,8 +190,8 @@ void lbpc_destroy(lbpc_ctx* c);
  *
  * It runs the same kernels as lbpc_step and lbpc_step_async, with the split organisation.
  *
- *   p         parameters, as for lbpc_create; nx * ny must not exceed LBPC_STATIC_MAX_NODES
- *             (LBPC_ENOMEM otherwise, before any device work)
+ *   p         parameters, as for lbpc_create, with prec LBPC_FP64 or LBPC_FP32; nx * ny must not
+ *             exceed LBPC_STATIC_MAX_NODES (LBPC_ENOMEM otherwise, before any device work)
  *   f_in,g_in post-collision populations of the previous step, device, [9][ny][nx] of the storage type
  *             (lbpc_params.prec), D2Q9 order as for lbpc_populations; slot a of node x holds the value
  *             that node x + e_a receives when it streams. A context's state has this form.

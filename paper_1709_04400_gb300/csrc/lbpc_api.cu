@@ -24,6 +24,7 @@ struct lbpc_ctx {
   SplitBuffers buf;
   int cur;              // buffer holding the current state
   int path;             // lbpc_path
+  size_t stage_bytes;   // bytes of one A/B half (f and g): the FP64 staging room between steps
   long long step;
   int initialised;
   cudaEvent_t ev[8];    // created on first lbpc_step_timed
@@ -57,7 +58,7 @@ void set_msg(char* dst, size_t n, const char* fmt, ...) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t f[2], g[2], phi, planes, partials, scalars, status, total;
+  size_t f[2], g[2], ref_f[2], ref_g[2], phi, planes, partials, scalars, status, total;
   size_t store, real;
   long long N;
   int nblocks;
@@ -66,7 +67,7 @@ struct Layout {
 Layout layout_of(const lbpc_params* p) {
   Layout L{};
   L.N = (long long)p->nx * p->ny;
-  L.store = p->prec == LBPC_FP64 ? 8 : 4;
+  L.store = p->prec == LBPC_FP64 ? 8 : (p->prec == LBPC_FP32 ? 4 : 2);
   L.real = p->prec == LBPC_FP64 ? 8 : 4;
   L.nblocks = (int)((L.N + lbpc::split_block() - 1) / lbpc::split_block());
   size_t off = 0;
@@ -76,6 +77,11 @@ Layout layout_of(const lbpc_params* p) {
   L.g[0] = off; off += pop;
   L.f[1] = off; off += pop;
   L.g[1] = off; off += pop;
+  const size_t ref = p->prec == LBPC_FP16DEV ? align256((size_t)L.N * sizeof(float)) : 0;
+  for (int k = 0; k < 2; ++k) {
+    L.ref_f[k] = off; off += ref;
+    L.ref_g[k] = off; off += ref;
+  }
   L.phi = off; off += align256((size_t)L.N * L.real);
   L.planes = off; off += (size_t)lbpc::split_nplanes() * align256((size_t)L.N * L.real);
   L.partials = off; off += align256(2 * (size_t)L.nblocks * sizeof(double));
@@ -139,6 +145,14 @@ template <class R> void fill_coefs(lbpc::Coefs<R>& c, const lbpc_params* p) {
   c.inv_cV = (R)(1.0 / p->cV);
   c.psi_scale = (R)(2.0 / p->G);
   c.cV_chi = (R)(p->cV * p->chi);
+  // rest-state equilibrium weights: f at rest is w_a rho; g at rest is M^{-1} m_eq(T, 0), which for
+  // Eq. 53 (m2_eq = 2T) is (5/9, 1/18 x8) and for Eq. 44 (m2_eq = T) the D2Q9 weights
+  const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+  const double wi[9] = {5.0 / 9, 1.0 / 18, 1.0 / 18, 1.0 / 18, 1.0 / 18, 1.0 / 18, 1.0 / 18, 1.0 / 18, 1.0 / 18};
+  for (int k = 0; k < 9; ++k) {
+    c.wf[k] = (R)w[k];
+    c.wg[k] = (R)(p->model == LBPC_IMPROVED ? wi[k] : w[k]);
+  }
 }
 
 DevParams make_dev_params(const lbpc_params* p) {
@@ -216,7 +230,7 @@ LBPC_API lbpc_status lbpc_check_params(const lbpc_params* p, char* msg, size_t n
   if (!p) BAD("params is NULL");
   if (p->nx < 2 || p->ny < 2) BAD("grid %d x %d: nx and ny must be >= 2", p->nx, p->ny);
   if ((long long)p->nx * p->ny > (1ll << 31)) BAD("grid %d x %d exceeds 2^31 nodes", p->nx, p->ny);
-  if (p->prec != LBPC_FP64 && p->prec != LBPC_FP32) BAD("prec %d unknown", p->prec);
+  if (p->prec != LBPC_FP64 && p->prec != LBPC_FP32 && p->prec != LBPC_FP16DEV) BAD("prec %d unknown", p->prec);
   if (p->model != LBPC_IMPROVED && p->model != LBPC_COMPROMISED) BAD("model %d unknown", p->model);
   if (p->lambda_mode != LBPC_LAMBDA_CONST && p->lambda_mode != LBPC_LAMBDA_RHO_CV_CHI) BAD("lambda_mode %d unknown", p->lambda_mode);
   if (p->flow_bc[0] != LBPC_PERIODIC || p->flow_bc[1] != LBPC_PERIODIC) BAD("x edges must be periodic");
@@ -324,7 +338,10 @@ LBPC_API lbpc_status lbpc_create(const lbpc_params* p, void* ws, size_t bytes, v
   for (int k = 0; k < 2; ++k) {
     c->buf.f[k] = base + L.f[k];
     c->buf.g[k] = base + L.g[k];
+    c->buf.ref_f[k] = p->prec == LBPC_FP16DEV ? (float*)(base + L.ref_f[k]) : nullptr;
+    c->buf.ref_g[k] = p->prec == LBPC_FP16DEV ? (float*)(base + L.ref_g[k]) : nullptr;
   }
+  c->stage_bytes = 2 * (L.g[0] - L.f[0]);
   c->buf.phi_prev = base + L.phi;
   const size_t plane = align256((size_t)L.N * L.real);
   for (int k = 0; k < lbpc::split_nplanes(); ++k) c->buf.planes[k] = base + L.planes + k * plane;
@@ -375,7 +392,7 @@ LBPC_API lbpc_status lbpc_init(lbpc_ctx* c, const double* rho, const double* T, 
 }
 
 static bool use_fused(const lbpc_ctx* c) {
-  return c->path == LBPC_PATH_FUSED || (c->path == LBPC_PATH_AUTO && c->p.prec == LBPC_FP32);
+  return c->path == LBPC_PATH_FUSED || (c->path == LBPC_PATH_AUTO && c->p.prec != LBPC_FP64);
 }
 
 static cudaError_t launch_step(lbpc_ctx* c, cudaEvent_t* ev) {
@@ -508,11 +525,27 @@ LBPC_API lbpc_status lbpc_populations(lbpc_ctx* c, double* f, double* g, int on_
   DeviceGuard dg(c->device);
   const size_t nb = 9 * (size_t)c->dp.N * sizeof(double);
   double* outs[2] = {f, g};
+  const size_t plane = (size_t)c->dp.N * sizeof(double);
   for (int which = 0; which < 2; ++which) {
     if (!outs[which]) continue;
-    double* dst = on_device ? outs[which] : (double*)dead_half(c);
-    CU(c, lbpc::split_export_pops(c->buf, c->dp, c->p.prec, c->cur, which, dst, c->stream), "lbpc_populations kernel");
-    if (!on_device) CU(c, cudaMemcpyAsync(outs[which], dst, nb, cudaMemcpyDeviceToHost, c->stream), "lbpc_populations D2H");
+    if (on_device) {
+      CU(c, lbpc::split_export_pops(c->buf, c->dp, c->p.prec, c->cur, which, -1, outs[which], c->stream),
+         "lbpc_populations kernel");
+    } else if (c->stage_bytes >= nb) {  // all 9 planes through the dead half at once
+      double* dst = (double*)dead_half(c);
+      CU(c, lbpc::split_export_pops(c->buf, c->dp, c->p.prec, c->cur, which, -1, dst, c->stream),
+         "lbpc_populations kernel");
+      CU(c, cudaMemcpyAsync(outs[which], dst, nb, cudaMemcpyDeviceToHost, c->stream), "lbpc_populations D2H");
+    } else {  // narrow storage: one plane at a time
+      double* dst = (double*)dead_half(c);
+      for (int a = 0; a < 9; ++a) {
+        CU(c, lbpc::split_export_pops(c->buf, c->dp, c->p.prec, c->cur, which, a, dst, c->stream),
+           "lbpc_populations kernel");
+        CU(c, cudaMemcpyAsync(outs[which] + (size_t)a * c->dp.N, dst, plane, cudaMemcpyDeviceToHost, c->stream),
+           "lbpc_populations D2H");
+        CU(c, cudaStreamSynchronize(c->stream), "lbpc_populations sync");
+      }
+    }
     CU(c, cudaStreamSynchronize(c->stream), "lbpc_populations sync");
   }
   return LBPC_OK;

@@ -7,6 +7,7 @@
 // MRT basis of Eqs. 42-43, whose thermal equilibria are Eq. 53.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -34,6 +35,8 @@ template <class R> struct Coefs {
   R inv_cV;     // 1 / c_V
   R psi_scale;  // 2 / G: psi^2 = (2/G) (p - rho c_s^2)
   R cV_chi;     // c_V chi
+  R wf[9];      // rest-state equilibrium weights of f: M^{-1} m_eq(1, v = 0) = (4/9, 1/9 x4, 1/36 x4)
+  R wg[9];      // rest-state equilibrium weights of g: M^{-1} m_eq(T = 1, v = 0) of the thermal model
 };
 
 // Everything a kernel needs, derived once on the host from lbpc_params and passed by value.
@@ -128,14 +131,54 @@ template <class R> __device__ __forceinline__ void eos(R rho, R T, const DevPara
 }
 
 // ------------------------------------------------------------------------------------------------
+// population storage
+// ------------------------------------------------------------------------------------------------
+// One population set (f or g) in one buffer: SoA [9][N] of the storage type S. With S = __half the
+// stored value is the deviation of the post-collision population from the rest-state equilibrium
+// w_a * ref of the node that stored it, ref being that node's density (f) or post-collision
+// temperature (g), held in an FP32 plane beside the populations. The collision conserves the zeroth
+// moment, so the deviations are of order |u| w rho and keep binary16's 11 bits relative to them.
+template <class S> struct PopBuf {
+  S* p;
+  float* ref;  // FP16 storage only
+};
+
+template <class S> struct is_half_t { static constexpr bool value = false; };
+template <> struct is_half_t<__half> { static constexpr bool value = true; };
+
+template <class S, class R>
+__device__ __forceinline__ R pop_load(const PopBuf<S>& b, long long N, int a, long long idx, const R* w) {
+  if constexpr (is_half_t<S>::value) {
+    return R(__half2float(__ldg(b.p + (long long)a * N + idx))) + w[a] * R(__ldg(b.ref + idx));
+  } else {
+    return R(__ldg(b.p + (long long)a * N + idx));
+  }
+}
+
+// Store the post-collision populations v of node i; refval is the node's zeroth moment after the
+// collision (rho for f, T + S0 for g), the reference of the FP16 deviation.
+template <class S, class R>
+__device__ __forceinline__ void pop_store(const PopBuf<S>& b, long long N, long long i, const R v[9], R refval,
+                                          const R* w) {
+  if constexpr (is_half_t<S>::value) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) b.p[(long long)a * N + i] = __float2half_rn(float(v[a] - w[a] * refval));
+    b.ref[i] = float(refval);
+  } else {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) b.p[(long long)a * N + i] = (S)v[a];
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
 // pull-stream with the boundary closures applied at the pulling node
 // ------------------------------------------------------------------------------------------------
 __device__ __forceinline__ int wrapx(int x, int nx) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); }
 
-// Post-stream population a at (x, y): src holds post-collision populations (SoA [9][N]); a
+// Post-stream populations at (x, y): src holds post-collision populations (SoA [9][N]); a
 // population whose source node lies beyond a non-periodic y edge is unknown and returned as 0.
 template <class S, class R>
-__device__ __forceinline__ void pull(const S* __restrict__ src, const DevParams& P, int x, int y, R v[9]) {
+__device__ __forceinline__ void pull(const PopBuf<S>& src, const R* w, const DevParams& P, int x, int y, R v[9]) {
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     const int sx = wrapx(x - EX(a), P.nx);
@@ -146,7 +189,7 @@ __device__ __forceinline__ void pull(const S* __restrict__ src, const DevParams&
       v[a] = R(0);
       continue;
     }
-    v[a] = R(__ldg(src + (long long)a * P.N + (long long)sy * P.nx + sx));
+    v[a] = pop_load<S, R>(src, P.N, a, (long long)sy * P.nx + sx, w);
   }
 }
 
@@ -243,10 +286,11 @@ template <class R> __device__ __forceinline__ void heat_closure(R g[9], const De
 
 // Post-stream, post-boundary f and g at (x, y).
 template <class S, class R>
-__device__ __forceinline__ void pull_closed(const S* __restrict__ fsrc, const S* __restrict__ gsrc, const DevParams& P,
-                                            int x, int y, R f[9], R g[9]) {
-  pull<S, R>(fsrc, P, x, y, f);
-  pull<S, R>(gsrc, P, x, y, g);
+__device__ __forceinline__ void pull_closed(const PopBuf<S>& fsrc, const PopBuf<S>& gsrc, const DevParams& P, int x,
+                                            int y, R f[9], R g[9]) {
+  const Coefs<R>& C = coefs<R>(P);
+  pull<S, R>(fsrc, C.wf, P, x, y, f);
+  pull<S, R>(gsrc, C.wg, P, x, y, g);
   flow_closure(f, P, y);
   heat_closure(g, P, x, y);
 }

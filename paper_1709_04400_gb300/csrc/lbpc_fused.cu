@@ -26,9 +26,10 @@ __device__ __forceinline__ int wrap_any(int x, int n) {
 
 // Post-stream populations of an interior node (no wrap, no closure): src[a][i - e_a].
 template <class S, class R>
-__device__ __forceinline__ void pull_interior(const S* __restrict__ src, long long N, int nx, long long i, R v[9]) {
+__device__ __forceinline__ void pull_interior(const PopBuf<S>& src, const R* w, long long N, int nx, long long i,
+                                              R v[9]) {
 #pragma unroll
-  for (int a = 0; a < 9; ++a) v[a] = R(__ldg(src + (long long)a * N + i - (long long)EY(a) * nx - EX(a)));
+  for (int a = 0; a < 9; ++a) v[a] = pop_load<S, R>(src, N, a, i - (long long)EY(a) * nx - EX(a), w);
 }
 
 // Domain row for region row offset: wraps when y is periodic, else clamps to the edge row.
@@ -48,8 +49,8 @@ template <class R, int TX, int TY> struct FusedSmem {
 // INTERIOR: the tile, its 2-ring and their pull sources lie inside the domain away from every edge,
 // so no index wraps, no boundary closure applies and no ghost row exists (a per-CTA, uniform choice).
 template <bool INTERIOR, class S, class R, int TX, int TY>
-__device__ __forceinline__ void fused_body(const S* __restrict__ fsrc, const S* __restrict__ gsrc,
-                                           S* __restrict__ fdst, S* __restrict__ gdst, R* __restrict__ phi_prev,
+__device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S>& gsrc, const PopBuf<S>& fdst,
+                                           const PopBuf<S>& gdst, R* __restrict__ phi_prev,
                                            const DevParams& P, long long step, int first,
                                            const double* __restrict__ rho_ave, double* __restrict__ partials,
                                            long long* __restrict__ status, FusedSmem<R, TX, TY>& sm) {
@@ -78,8 +79,8 @@ __device__ __forceinline__ void fused_body(const S* __restrict__ fsrc, const S* 
   R f[9], g[9];
   if (INTERIOR) {
     const long long io = (long long)gy * P.nx + gx;
-    pull_interior<S, R>(fsrc, P.N, P.nx, io, f);
-    pull_interior<S, R>(gsrc, P.N, P.nx, io, g);
+    pull_interior<S, R>(fsrc, C.wf, P.N, P.nx, io, f);
+    pull_interior<S, R>(gsrc, C.wg, P.N, P.nx, io, g);
   } else {
     pull_closed<S, R>(fsrc, gsrc, P, mx, my, f, g);
   }
@@ -118,8 +119,8 @@ __device__ __forceinline__ void fused_body(const S* __restrict__ fsrc, const S* 
     R fr[9], gr[9];
     if (INTERIOR) {
       const long long io = (long long)(y0 + hy - 2) * P.nx + (x0 + hx - 2);
-      pull_interior<S, R>(fsrc, P.N, P.nx, io, fr);
-      pull_interior<S, R>(gsrc, P.N, P.nx, io, gr);
+      pull_interior<S, R>(fsrc, C.wf, P.N, P.nx, io, fr);
+      pull_interior<S, R>(gsrc, C.wg, P.N, P.nx, io, gr);
     } else {
       const int x = wrap_any(x0 + hx - 2, P.nx), y = row_of(P, y0 + hy - 2);
       pull_closed<S, R>(fsrc, gsrc, P, x, y, fr, gr);
@@ -244,16 +245,12 @@ __device__ __forceinline__ void fused_body(const S* __restrict__ fsrc, const S* 
   phi_prev[i] = phi;
   collide_flow(f, rho, vx, vy, Fx, Fy, Q, P);
   collide_heat(g, T, vx, vy, S0, P);
-#pragma unroll
-  for (int a = 0; a < 9; ++a) {
-    fdst[(long long)a * P.N + i] = (S)f[a];
-    gdst[(long long)a * P.N + i] = (S)g[a];
-  }
+  pop_store<S, R>(fdst, P.N, i, f, rho, C.wf);
+  pop_store<S, R>(gdst, P.N, i, g, T + S0, C.wg);
 }
 
 template <class S, class R, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY) k_fused(const S* __restrict__ fsrc, const S* __restrict__ gsrc,
-                                                   S* __restrict__ fdst, S* __restrict__ gdst,
+__global__ void __launch_bounds__(TX* TY) k_fused(PopBuf<S> fsrc, PopBuf<S> gsrc, PopBuf<S> fdst, PopBuf<S> gdst,
                                                    R* __restrict__ phi_prev, DevParams P, long long step, int first,
                                                    const double* __restrict__ rho_ave, double* __restrict__ partials,
                                                    long long* __restrict__ status) {
@@ -272,9 +269,10 @@ static cudaError_t fused_impl(const SplitBuffers& b, const DevParams& P, int cur
                               cudaEvent_t* ev) {
   dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
   if (ev) cudaEventRecord(ev[0], st);
-  k_fused<S, R, TX, TY><<<grid, TX * TY, 0, st>>>((const S*)b.f[cur], (const S*)b.g[cur], (S*)b.f[cur ^ 1],
-                                                  (S*)b.g[cur ^ 1], (R*)b.phi_prev, P, step, step == 0, b.scalars,
-                                                  b.partials, b.status);
+  k_fused<S, R, TX, TY><<<grid, TX * TY, 0, st>>>(
+      PopBuf<S>{(S*)b.f[cur], b.ref_f[cur]}, PopBuf<S>{(S*)b.g[cur], b.ref_g[cur]},
+      PopBuf<S>{(S*)b.f[cur ^ 1], b.ref_f[cur ^ 1]}, PopBuf<S>{(S*)b.g[cur ^ 1], b.ref_g[cur ^ 1]}, (R*)b.phi_prev, P,
+      step, step == 0, b.scalars, b.partials, b.status);
   if (ev) cudaEventRecord(ev[1], st);
   if (P.buoyancy) {
     fused_finish(b, P, (int)(grid.x * grid.y), st);
@@ -285,8 +283,9 @@ static cudaError_t fused_impl(const SplitBuffers& b, const DevParams& P, int cur
 
 cudaError_t fused_step(const SplitBuffers& b, const DevParams& P, int prec, int cur, long long step, cudaStream_t st,
                        cudaEvent_t* ev) {
-  return prec == 0 ? fused_impl<double, double, 32, 8>(b, P, cur, step, st, ev)
-                   : fused_impl<float, float, 32, 16>(b, P, cur, step, st, ev);
+  if (prec == 0) return fused_impl<double, double, 32, 8>(b, P, cur, step, st, ev);
+  if (prec == 1) return fused_impl<float, float, 32, 16>(b, P, cur, step, st, ev);
+  return fused_impl<__half, float, 32, 16>(b, P, cur, step, st, ev);
 }
 
 }  // namespace lbpc

@@ -11,6 +11,8 @@ namespace lbpc {
 struct SplitBuffers {
   void* f[2];        // populations f, post-collision layout, A/B (storage type)
   void* g[2];        // populations g
+  float* ref_f[2];   // FP16 storage: per-node reference density of the stored f deviations (A/B)
+  float* ref_g[2];   // FP16 storage: per-node reference temperature of the stored g deviations (A/B)
   void* phi_prev;    // phi(t - dt), arithmetic type
   void* planes[16];  // scratch planes of the split kernels, arithmetic type
   double* partials;  // 2 * nblocks per-block partial sums
@@ -28,8 +30,9 @@ cudaError_t split_init(const SplitBuffers& b, const DevParams& P, int prec, cons
 cudaError_t split_sums(const SplitBuffers& b, const DevParams& P, int prec, int cur, cudaStream_t st);
 cudaError_t split_fields(const SplitBuffers& b, const DevParams& P, int prec, int cur, long long step, double* rho,
                          double* ux, double* uy, double* T, cudaStream_t st);
-cudaError_t split_export_pops(const SplitBuffers& b, const DevParams& P, int prec, int cur, int which, double* out,
-                              cudaStream_t st);
+// which = 0: f, 1: g; only < 0: all 9 planes [9][N], else plane `only` into out[N].
+cudaError_t split_export_pops(const SplitBuffers& b, const DevParams& P, int prec, int cur, int which, int only,
+                              double* out, cudaStream_t st);
 int split_nplanes();
 int split_block();
 

@@ -65,7 +65,7 @@ template <class R> __device__ __forceinline__ R lap(const R c[3][3]) {
 }
 
 template <class S, class R>
-__global__ void __launch_bounds__(BLOCK) k_macro(const S* __restrict__ fsrc, const S* __restrict__ gsrc, Planes<R> pl,
+__global__ void __launch_bounds__(BLOCK) k_macro(PopBuf<S> fsrc, PopBuf<S> gsrc, Planes<R> pl,
                                                  DevParams P, long long step, int do_partials,
                                                  double* __restrict__ partials, long long* __restrict__ status) {
   __shared__ double red[BLOCK / 32];
@@ -141,9 +141,8 @@ __global__ void __launch_bounds__(BLOCK) k_force(Planes<R> pl, DevParams P, cons
 // roles share no data (both read the scratch planes), so a node's work splits into two independent
 // chains and twice as many warps hide the FP64 latency on small grids.
 template <class S, class R>
-__global__ void __launch_bounds__(2 * BLOCK) k_collide(const S* __restrict__ fsrc, const S* __restrict__ gsrc,
-                                                       S* __restrict__ fdst, S* __restrict__ gdst, Planes<R> pl,
-                                                       R* __restrict__ phi_prev, DevParams P, int first) {
+__global__ void __launch_bounds__(2 * BLOCK) k_collide(PopBuf<S> fsrc, PopBuf<S> gsrc, PopBuf<S> fdst, PopBuf<S> gdst,
+                                                       Planes<R> pl, R* __restrict__ phi_prev, DevParams P, int first) {
   const Coefs<R>& C = coefs<R>(P);
   const bool heat = threadIdx.x >= BLOCK;
   const long long i = (long long)blockIdx.x * BLOCK + (threadIdx.x - (heat ? BLOCK : 0));
@@ -152,15 +151,15 @@ __global__ void __launch_bounds__(2 * BLOCK) k_collide(const S* __restrict__ fsr
   const R vx = pl.p[P_VX][i], vy = pl.p[P_VY][i];
   if (!heat) {
     R f[9];
-    pull<S, R>(fsrc, P, x, y, f);
+    pull<S, R>(fsrc, C.wf, P, x, y, f);
     flow_closure(f, P, y);
-    collide_flow(f, pl.p[P_RHO][i], vx, vy, pl.p[P_FX][i], pl.p[P_FY][i], pl.p[P_Q][i], P);
-#pragma unroll
-    for (int a = 0; a < 9; ++a) fdst[(long long)a * P.N + i] = (S)f[a];
+    const R rho = pl.p[P_RHO][i];
+    collide_flow(f, rho, vx, vy, pl.p[P_FX][i], pl.p[P_FY][i], pl.p[P_Q][i], P);
+    pop_store<S, R>(fdst, P.N, i, f, rho, C.wf);
     return;
   }
   R g[9];
-  pull<S, R>(gsrc, P, x, y, g);
+  pull<S, R>(gsrc, C.wg, P, x, y, g);
   heat_closure(g, P, x, y);
   const R rho = pl.p[P_RHO][i];
   const R T = pl.p[P_T][i];
@@ -190,8 +189,7 @@ __global__ void __launch_bounds__(2 * BLOCK) k_collide(const S* __restrict__ fsr
   }
   phi_prev[i] = phi;
   collide_heat(g, T, vx, vy, S0, P);
-#pragma unroll
-  for (int a = 0; a < 9; ++a) gdst[(long long)a * P.N + i] = (S)g[a];
+  pop_store<S, R>(gdst, P.N, i, g, T + S0, C.wg);
 }
 
 // Fixed-order sum of the block partials: each thread accumulates a strided subset in order, then one
@@ -212,10 +210,11 @@ __global__ void __launch_bounds__(BLOCK) k_finish(const double* __restrict__ par
 template <class S>
 __global__ void __launch_bounds__(BLOCK) k_init(const double* __restrict__ rho_in, const double* __restrict__ T_in,
                                                 const double* __restrict__ ux_in, const double* __restrict__ uy_in,
-                                                S* __restrict__ f, S* __restrict__ g, DevParams P) {
+                                                PopBuf<S> f, PopBuf<S> g, DevParams P) {
   const long long i = (long long)blockIdx.x * BLOCK + threadIdx.x;
   if (i >= P.N) return;
   const int y = (int)(i / P.nx), x = (int)(i - (long long)y * P.nx);
+  double fv[9], gv[9];
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     // node whose pull reads slot (x, y) in direction a
@@ -223,8 +222,8 @@ __global__ void __launch_bounds__(BLOCK) k_init(const double* __restrict__ rho_i
     int ty = y + EY(a);
     if (ty < 0 || ty >= P.ny) {
       if (!P.yper) {  // no node pulls this slot; keep it finite
-        f[(long long)a * P.N + i] = (S)0.0;
-        g[(long long)a * P.N + i] = (S)0.0;
+        fv[a] = 0.0;
+        gv[a] = 0.0;
         continue;
       }
       ty = ty < 0 ? ty + P.ny : ty - P.ny;
@@ -240,14 +239,17 @@ __global__ void __launch_bounds__(BLOCK) k_init(const double* __restrict__ rho_i
     from_moments(m, fe);
     heat_meq(T, vx, vy, P.model, m);
     from_moments(m, ge);
-    f[(long long)a * P.N + i] = (S)fe[a];
-    g[(long long)a * P.N + i] = (S)ge[a];
+    fv[a] = fe[a];
+    gv[a] = ge[a];
   }
+  // FP16 storage: deviations from the rest equilibrium of this slot's own node
+  pop_store<S, double>(f, P.N, i, fv, rho_in[i], P.cd.wf);
+  pop_store<S, double>(g, P.N, i, gv, T_in[i], P.cd.wg);
 }
 
 // Sums of rho and T over the current (post-boundary) state into per-block partials.
 template <class S>
-__global__ void __launch_bounds__(BLOCK) k_sums(const S* __restrict__ fsrc, const S* __restrict__ gsrc, DevParams P,
+__global__ void __launch_bounds__(BLOCK) k_sums(PopBuf<S> fsrc, PopBuf<S> gsrc, DevParams P,
                                                 double* __restrict__ partials, int stride) {
   __shared__ double red[BLOCK / 32];
   const long long i = (long long)blockIdx.x * BLOCK + threadIdx.x;
@@ -267,13 +269,17 @@ __global__ void __launch_bounds__(BLOCK) k_sums(const S* __restrict__ fsrc, cons
 
 // Post-boundary populations of the current state as FP64 [9][N] (which = 0: f, 1: g).
 template <class S>
-__global__ void __launch_bounds__(BLOCK) k_export_pops(const S* __restrict__ fsrc, const S* __restrict__ gsrc,
-                                                       DevParams P, int which, double* __restrict__ out) {
+__global__ void __launch_bounds__(BLOCK) k_export_pops(PopBuf<S> fsrc, PopBuf<S> gsrc, DevParams P, int which,
+                                                       int only, double* __restrict__ out) {
   const long long i = (long long)blockIdx.x * BLOCK + threadIdx.x;
   if (i >= P.N) return;
   const int y = (int)(i / P.nx), x = (int)(i - (long long)y * P.nx);
   double f[9], g[9];
   pull_closed<S, double>(fsrc, gsrc, P, x, y, f, g);
+  if (only >= 0) {  // one population plane into out[N]
+    out[i] = which ? g[only] : f[only];
+    return;
+  }
 #pragma unroll
   for (int a = 0; a < 9; ++a) out[(long long)a * P.N + i] = which ? g[a] : f[a];
 }
@@ -301,19 +307,21 @@ template <class S, class R> static Planes<R> planes_of(const SplitBuffers& b) {
   return pl;
 }
 
+template <class S> static PopBuf<S> fbuf(const SplitBuffers& b, int k) { return PopBuf<S>{(S*)b.f[k], b.ref_f[k]}; }
+template <class S> static PopBuf<S> gbuf(const SplitBuffers& b, int k) { return PopBuf<S>{(S*)b.g[k], b.ref_g[k]}; }
+
 template <class S, class R>
 static cudaError_t step_impl(const SplitBuffers& b, const DevParams& P, int cur, long long step, cudaStream_t st,
                              cudaEvent_t* ev) {
   const unsigned nb = blocks_for(P.N);
-  const S* fs = (const S*)b.f[cur];
-  const S* gs = (const S*)b.g[cur];
   Planes<R> pl = planes_of<S, R>(b);
   if (ev) cudaEventRecord(ev[0], st);
-  k_macro<S, R><<<nb, BLOCK, 0, st>>>(fs, gs, pl, P, step, P.buoyancy, b.partials, b.status);
+  k_macro<S, R><<<nb, BLOCK, 0, st>>>(fbuf<S>(b, cur), gbuf<S>(b, cur), pl, P, step, P.buoyancy, b.partials, b.status);
   if (ev) cudaEventRecord(ev[1], st);
   k_force<R><<<nb, BLOCK, 0, st>>>(pl, P, b.scalars);
   if (ev) cudaEventRecord(ev[2], st);
-  k_collide<S, R><<<nb, 2 * BLOCK, 0, st>>>(fs, gs, (S*)b.f[cur ^ 1], (S*)b.g[cur ^ 1], pl, (R*)b.phi_prev, P, step == 0);
+  k_collide<S, R><<<nb, 2 * BLOCK, 0, st>>>(fbuf<S>(b, cur), gbuf<S>(b, cur), fbuf<S>(b, cur ^ 1), gbuf<S>(b, cur ^ 1),
+                                            pl, (R*)b.phi_prev, P, step == 0);
   if (ev) cudaEventRecord(ev[3], st);
   if (P.buoyancy) {
     k_finish<<<1, BLOCK, 0, st>>>(b.partials, (int)nb, 0, 1, 1.0 / (double)P.N, b.scalars);
@@ -324,7 +332,9 @@ static cudaError_t step_impl(const SplitBuffers& b, const DevParams& P, int cur,
 
 cudaError_t split_step(const SplitBuffers& b, const DevParams& P, int prec, int cur, long long step, cudaStream_t st,
                        cudaEvent_t* ev) {
-  return prec == 0 ? step_impl<double, double>(b, P, cur, step, st, ev) : step_impl<float, float>(b, P, cur, step, st, ev);
+  if (prec == 0) return step_impl<double, double>(b, P, cur, step, st, ev);
+  if (prec == 1) return step_impl<float, float>(b, P, cur, step, st, ev);
+  return step_impl<__half, float>(b, P, cur, step, st, ev);
 }
 
 int split_kernel_count(const DevParams& P) { return P.buoyancy ? 4 : 3; }
@@ -338,28 +348,32 @@ template <class S>
 static cudaError_t init_impl(const SplitBuffers& b, const DevParams& P, const double* rho, const double* T,
                              const double* ux, const double* uy, cudaStream_t st) {
   const unsigned nb = blocks_for(P.N);
-  k_init<S><<<nb, BLOCK, 0, st>>>(rho, T, ux, uy, (S*)b.f[0], (S*)b.g[0], P);
+  k_init<S><<<nb, BLOCK, 0, st>>>(rho, T, ux, uy, fbuf<S>(b, 0), gbuf<S>(b, 0), P);
   // rho_ave of the initial (post-boundary) state
-  k_sums<S><<<nb, BLOCK, 0, st>>>((const S*)b.f[0], (const S*)b.g[0], P, b.partials, (int)nb);
+  k_sums<S><<<nb, BLOCK, 0, st>>>(fbuf<S>(b, 0), gbuf<S>(b, 0), P, b.partials, (int)nb);
   k_finish<<<1, BLOCK, 0, st>>>(b.partials, (int)nb, (int)nb, 1, 1.0 / (double)P.N, b.scalars);
   return cudaGetLastError();
 }
 
 cudaError_t split_init(const SplitBuffers& b, const DevParams& P, int prec, const double* rho, const double* T,
                        const double* ux, const double* uy, cudaStream_t st) {
-  return prec == 0 ? init_impl<double>(b, P, rho, T, ux, uy, st) : init_impl<float>(b, P, rho, T, ux, uy, st);
+  if (prec == 0) return init_impl<double>(b, P, rho, T, ux, uy, st);
+  if (prec == 1) return init_impl<float>(b, P, rho, T, ux, uy, st);
+  return init_impl<__half>(b, P, rho, T, ux, uy, st);
 }
 
 template <class S>
 static cudaError_t sums_impl(const SplitBuffers& b, const DevParams& P, int cur, cudaStream_t st) {
   const unsigned nb = blocks_for(P.N);
-  k_sums<S><<<nb, BLOCK, 0, st>>>((const S*)b.f[cur], (const S*)b.g[cur], P, b.partials, (int)nb);
+  k_sums<S><<<nb, BLOCK, 0, st>>>(fbuf<S>(b, cur), gbuf<S>(b, cur), P, b.partials, (int)nb);
   k_finish<<<1, BLOCK, 0, st>>>(b.partials, (int)nb, (int)nb, 2, 1.0, b.scalars + 1);
   return cudaGetLastError();
 }
 
 cudaError_t split_sums(const SplitBuffers& b, const DevParams& P, int prec, int cur, cudaStream_t st) {
-  return prec == 0 ? sums_impl<double>(b, P, cur, st) : sums_impl<float>(b, P, cur, st);
+  if (prec == 0) return sums_impl<double>(b, P, cur, st);
+  if (prec == 1) return sums_impl<float>(b, P, cur, st);
+  return sums_impl<__half>(b, P, cur, st);
 }
 
 template <class S, class R>
@@ -367,7 +381,7 @@ static cudaError_t fields_impl(const SplitBuffers& b, const DevParams& P, int cu
                                double* ux, double* uy, double* T, cudaStream_t st) {
   const unsigned nb = blocks_for(P.N);
   Planes<R> pl = planes_of<S, R>(b);
-  k_macro<S, R><<<nb, BLOCK, 0, st>>>((const S*)b.f[cur], (const S*)b.g[cur], pl, P, step, 0, b.partials, b.status);
+  k_macro<S, R><<<nb, BLOCK, 0, st>>>(fbuf<S>(b, cur), gbuf<S>(b, cur), pl, P, step, 0, b.partials, b.status);
   k_force<R><<<nb, BLOCK, 0, st>>>(pl, P, b.scalars);
   k_export_fields<R><<<nb, BLOCK, 0, st>>>(pl, P, rho, ux, uy, T);
   return cudaGetLastError();
@@ -375,17 +389,20 @@ static cudaError_t fields_impl(const SplitBuffers& b, const DevParams& P, int cu
 
 cudaError_t split_fields(const SplitBuffers& b, const DevParams& P, int prec, int cur, long long step, double* rho,
                          double* ux, double* uy, double* T, cudaStream_t st) {
-  return prec == 0 ? fields_impl<double, double>(b, P, cur, step, rho, ux, uy, T, st)
-                   : fields_impl<float, float>(b, P, cur, step, rho, ux, uy, T, st);
+  if (prec == 0) return fields_impl<double, double>(b, P, cur, step, rho, ux, uy, T, st);
+  if (prec == 1) return fields_impl<float, float>(b, P, cur, step, rho, ux, uy, T, st);
+  return fields_impl<__half, float>(b, P, cur, step, rho, ux, uy, T, st);
 }
 
-cudaError_t split_export_pops(const SplitBuffers& b, const DevParams& P, int prec, int cur, int which, double* out,
-                              cudaStream_t st) {
+cudaError_t split_export_pops(const SplitBuffers& b, const DevParams& P, int prec, int cur, int which, int only,
+                              double* out, cudaStream_t st) {
   const unsigned nb = blocks_for(P.N);
   if (prec == 0)
-    k_export_pops<double><<<nb, BLOCK, 0, st>>>((const double*)b.f[cur], (const double*)b.g[cur], P, which, out);
+    k_export_pops<double><<<nb, BLOCK, 0, st>>>(fbuf<double>(b, cur), gbuf<double>(b, cur), P, which, only, out);
+  else if (prec == 1)
+    k_export_pops<float><<<nb, BLOCK, 0, st>>>(fbuf<float>(b, cur), gbuf<float>(b, cur), P, which, only, out);
   else
-    k_export_pops<float><<<nb, BLOCK, 0, st>>>((const float*)b.f[cur], (const float*)b.g[cur], P, which, out);
+    k_export_pops<__half><<<nb, BLOCK, 0, st>>>(fbuf<__half>(b, cur), gbuf<__half>(b, cur), P, which, only, out);
   return cudaGetLastError();
 }
 

@@ -54,6 +54,7 @@ DevParams make_dev_params_public(const lbpc_params* p);
 LBPC_API lbpc_status lbpc_step_static(const lbpc_params* p, const void* f_in, const void* g_in, void* f_out,
                                       void* g_out, void* phi_prev, double* rho_ave, int64_t step, void* stream) {
   if (lbpc_check_params(p, nullptr, 0) != LBPC_OK) return LBPC_EINVAL;
+  if (p->prec == LBPC_FP16DEV) return LBPC_EINVAL;  // FP16 storage needs reference planes this call does not take
   const long long N = (long long)p->nx * p->ny;
   if (N > kMaxNodes) return LBPC_ENOMEM;  // beyond the static scratch: use lbpc_create with a workspace
   if (!f_in || !g_in || !f_out || !g_out || !phi_prev || step < 0) return LBPC_EINVAL;
