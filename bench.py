@@ -35,7 +35,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="evaporation", choices=["evaporation", "droplet", "heated_wall"])
+    ap.add_argument("--workload", default="evaporation", choices=["evaporation", "droplet", "heated_wall", "batch"])
+    ap.add_argument("--instances", type=int, default=256, help="batched workload: number of instances")
     ap.add_argument("--n", type=int, default=0, help="grid side (0 = the workload's own size)")
     ap.add_argument("--dT", type=float, default=0.1, help="superheat dT / T_c of the evaporation case")
     ap.add_argument("--prec", default="", choices=["", "fp64", "fp32", "fp16"])
@@ -319,6 +320,92 @@ def run_native(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """Batched workload: many uneven evaporation instances in one persistent launch per step (graph
+    replayed), against the plain path (each instance stepped on its own through lbpc_step)."""
+    import numpy as np
+    import torch
+
+    from paper_1709_04400_gb300 import build, lbpc, workloads
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    build.build()
+    p0 = lbpc.Params(nx=8, ny=8)
+    Tc, _ = lbpc.eos_critical(p0)
+    rv, rl, _ = lbpc.coexistence(p0, 0.86 * Tc)
+    prec_name = args.prec or "fp32"
+    prec = {"fp64": lbpc.FP64, "fp32": lbpc.FP32, "fp16": lbpc.FP16DEV}[prec_name]
+    insts = workloads.batched_evaporation(Tc, rv, rl, count=args.instances)
+    params = [lbpc.params_from_case(c, prec) for c, _, _ in insts]
+    nodes = sum(p.nx * p.ny for p in params)
+    arena = sum(lbpc.Batch.instance_bytes(p) for p in params) + (256 << 20)
+    b = lbpc.Batch(prec, arena, max_instances=len(insts) + 8)
+    for p, (c, r, t) in zip(params, insts):
+        b.add(p, r, t)
+    tuned = b.autotune(steps_per_candidate=2)
+    b.step(args.warmup)
+    b.check()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(b.stream)
+        b.step(args.steps)
+        ev1.record(b.stream)
+        ev1.synchronize()
+    b.check()
+    batch_s = ev0.elapsed_time(ev1) / 1e3
+    cfg = b.config()
+    b.close()
+    # plain path: the same instances, each advanced on its own (fused kernel, one launch per step)
+    sims = []
+    for p, (c, r, t) in zip(params, insts):
+        sim = lbpc.Simulation(p)
+        sim.init(r, t)
+        sims.append(sim)
+    for sim in sims:
+        sim.step(args.warmup, sync=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for sim in sims:
+        sim.step(args.steps, sync=False)
+    e1.record()
+    e1.synchronize()
+    plain_s = e0.elapsed_time(e1) / 1e3
+    for sim in sims:
+        sim.check()
+        sim.close()
+    value = nodes * args.steps / batch_s / 1e6
+    plain = nodes * args.steps / plain_s / 1e6
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak_bw = float(peaks.get("hbm_gbs", 6800.0))
+    pb = {lbpc.FP64: 8, lbpc.FP32: 4, lbpc.FP16DEV: 2}[prec]
+    achieved = fused_bytes_per_node(pb) * nodes / (batch_s / args.steps) / 1e9
+    line = {
+        "metric": "batched coupled flow+thermal MLUPS (aggregate)", "value": value, "unit": "MLUPS", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": batch_s * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == lbpc.FP64 else "f32", "data": "synthetic",
+        "config": {"workload": f"batched_evaporation_{len(insts)}", "instances": len(insts), "nodes": nodes,
+                   "storage": prec_name, "tile": [cfg["tile_x"], cfg["tile_y"]], "ctas_per_sm": cfg["ctas_per_sm"],
+                   "graph_chunk": cfg["graph_chunk"], "autotune": tuned,
+                   "l2": "working set of %.1f GB exceeds L2" % (nodes * fused_bytes_per_node(pb) / 1e9)},
+        "plain_path": {"value": plain, "unit": "MLUPS", "ms_per_step": plain_s * 1e3 / args.steps,
+                       "how": "each instance stepped alone through lbpc_step (fused kernel, one launch per step)"},
+        "batched_over_plain": value / plain,
+        "roofline": {"bound": "hbm", "kernel": "k_batch_step", "achieved": achieved, "peak": peak_bw, "unit": "GB/s",
+                     "frac": achieved / peak_bw, "traffic": None, "bytes_per_node": fused_bytes_per_node(pb)},
+        "gpu_launches": 2 * args.steps, "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
@@ -357,4 +444,9 @@ if __name__ == "__main__":
     a = parse()
     if a.warmup < 3:
         a.warmup = 3
-    (run_reference if a.impl == "reference" else run_native)(a)
+    if a.impl == "reference":
+        run_reference(a)
+    elif a.workload == "batch":
+        run_batch(a)
+    else:
+        run_native(a)

@@ -178,6 +178,67 @@ const char* lbpc_last_error(const lbpc_ctx* c);
 void lbpc_destroy(lbpc_ctx* c);
 
 /* ------------------------------------------------------------------------------------------------
+ * Batches: many independent simulations of uneven size advancing together.
+ *
+ * The per-node arithmetic is the fused step's. Every instance of a batch advances in one persistent
+ * launch per step: CTAs walk a device-resident work list of (instance, tile) entries, one entry per
+ * tile of every instance. Steps are replayed through a captured CUDA graph in chunks when the batch
+ * has a non-default stream. Instances can join and leave between calls. Their parameters,
+ * boundaries, sizes and step counts are their own, and an instance's result does not depend on
+ * what else is in the batch. All instances of a batch share one storage precision.
+ *
+ * The batch takes one caller-owned device arena. The library carves every instance's state out of it
+ * with a first-fit allocator and allocates no device memory of its own.
+ * ------------------------------------------------------------------------------------------------ */
+typedef struct lbpc_batch lbpc_batch; /* opaque */
+
+/* Arena bytes one instance with these parameters takes (0 if the parameters are invalid). */
+size_t lbpc_batch_instance_bytes(const lbpc_params* p);
+
+/* Create an empty batch of at most max_instances instances in storage precision prec over the
+ * caller's arena (256-byte aligned, bytes long). Fixed descriptors take a small part of the arena. */
+lbpc_status lbpc_batch_create(int32_t prec, int32_t max_instances, void* d_arena, size_t bytes, void* stream,
+                              lbpc_batch** out);
+
+/* Add an instance started from the equilibrium of rho, T ([ny][nx] FP64, host or device), like
+ * lbpc_init. Writes its id. LBPC_ENOMEM when the arena or the slots are full. Synchronises. */
+lbpc_status lbpc_batch_add(lbpc_batch* b, const lbpc_params* p, const double* rho, const double* T, int on_device,
+                           int32_t* id);
+
+/* Remove an instance and return its memory to the arena. Synchronises. */
+lbpc_status lbpc_batch_remove(lbpc_batch* b, int32_t id);
+
+/* Enqueue n steps of every instance; does not synchronise (lbpc_batch_check reports errors). */
+lbpc_status lbpc_batch_step(lbpc_batch* b, int64_t n);
+
+/* Synchronise and check every instance's status word; LBPC_ENONPHYS names the first failed id. */
+lbpc_status lbpc_batch_check(lbpc_batch* b, int32_t* failed_id);
+
+/* Fields and domain sums of one instance, as lbpc_fields and lbpc_sums (scratch for the fields comes
+ * from the arena for the duration of the call). Synchronise. */
+lbpc_status lbpc_batch_fields(lbpc_batch* b, int32_t id, double* rho, double* ux, double* uy, double* T, int on_device);
+lbpc_status lbpc_batch_sums(lbpc_batch* b, int32_t id, double* mass, double* heat);
+
+/* Steps taken by instance id (-1 if no such instance). */
+int64_t lbpc_batch_step_count(const lbpc_batch* b, int32_t id);
+
+/* Tile shape (variant 0: 32x8, 1: 32x16, 2: 64x8) and persistent CTAs per SM of the step kernel. */
+lbpc_status lbpc_batch_set_config(lbpc_batch* b, int32_t variant, int32_t ctas_per_sm);
+lbpc_status lbpc_batch_config(const lbpc_batch* b, int32_t* tile_x, int32_t* tile_y, int32_t* ctas_per_sm,
+                              int32_t* graph_chunk);
+
+/* Time every tile shape and CTA count on the batch's own instances and keep the fastest. Every
+ * configuration computes the same step, so tuning advances the batch by real steps: one warm-up
+ * plus steps_per_candidate per candidate. */
+lbpc_status lbpc_batch_autotune(lbpc_batch* b, int32_t steps_per_candidate, int32_t* best_variant, int32_t* best_ctas,
+                                float* best_ms_per_step);
+
+/* Free bytes left in the arena, the last error message, and teardown (the arena stays the caller's). */
+size_t lbpc_batch_free_bytes(const lbpc_batch* b);
+const char* lbpc_batch_last_error(const lbpc_batch* b);
+void lbpc_batch_destroy(lbpc_batch* b);
+
+/* ------------------------------------------------------------------------------------------------
  * One time step without any device allocation.
  *
  * Some callers cannot allocate device memory at all: an application whose device memory is handed

@@ -53,7 +53,8 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
                                            const PopBuf<S>& gdst, R* __restrict__ phi_prev,
                                            const DevParams& P, long long step, int first,
                                            const double* __restrict__ rho_ave, double* __restrict__ partials,
-                                           long long* __restrict__ status, FusedSmem<R, TX, TY>& sm) {
+                                           long long* __restrict__ status, FusedSmem<R, TX, TY>& sm, int x0, int y0,
+                                           int pslot) {
   constexpr int RX = TX + 4, RY = TY + 4;  // stage-1 region (tile + 2)
   constexpr int VX = TX + 2, VY = TY + 2;  // stage-2 region (tile + 1)
   (void)RY;
@@ -70,7 +71,6 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
   const Coefs<R>& C = coefs<R>(P);
   const int t = threadIdx.x;
   const int tx = t % TX, ty = t / TX;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int gx = x0 + tx, gy = y0 + ty;
   const bool active = gx < P.nx && gy < P.ny;
   const int mx = wrap_any(gx, P.nx), my = row_of(P, gy);
@@ -138,7 +138,7 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
   }
   if (P.buoyancy) {
     const double sr = block_sum<NT>(active ? (double)rho : 0.0, s_red);
-    if (t == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = sr;
+    if (t == 0) partials[pslot] = sr;
   } else {
     __syncthreads();
   }
@@ -257,10 +257,13 @@ __global__ void __launch_bounds__(TX* TY) k_fused(PopBuf<S> fsrc, PopBuf<S> gsrc
   __shared__ FusedSmem<R, TX, TY> sm;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const bool interior = x0 >= 3 && x0 + TX + 3 <= P.nx && y0 >= 3 && y0 + TY + 3 <= P.ny;
+  const int pslot = blockIdx.y * gridDim.x + blockIdx.x;
   if (interior)
-    fused_body<true, S, R, TX, TY>(fsrc, gsrc, fdst, gdst, phi_prev, P, step, first, rho_ave, partials, status, sm);
+    fused_body<true, S, R, TX, TY>(fsrc, gsrc, fdst, gdst, phi_prev, P, step, first, rho_ave, partials, status, sm, x0,
+                                   y0, pslot);
   else
-    fused_body<false, S, R, TX, TY>(fsrc, gsrc, fdst, gdst, phi_prev, P, step, first, rho_ave, partials, status, sm);
+    fused_body<false, S, R, TX, TY>(fsrc, gsrc, fdst, gdst, phi_prev, P, step, first, rho_ave, partials, status, sm,
+                                    x0, y0, pslot);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -286,6 +289,107 @@ cudaError_t fused_step(const SplitBuffers& b, const DevParams& P, int prec, int 
   if (prec == 0) return fused_impl<double, double, 32, 8>(b, P, cur, step, st, ev);
   if (prec == 1) return fused_impl<float, float, 32, 16>(b, P, cur, step, st, ev);
   return fused_impl<__half, float, 32, 16>(b, P, cur, step, st, ev);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Batched step: many independent instances of uneven size in one persistent launch. CTAs walk a work
+// list of (instance, tile) entries round-robin; each tile runs the same body as the single-instance
+// kernel with that instance's parameters (copied to shared memory when the instance changes) and
+// buffers, so an instance's result does not depend on what else is in the batch. The tile count and
+// every per-instance value live in device memory, so a captured CUDA graph of these launches stays
+// valid when instances join or leave.
+// ------------------------------------------------------------------------------------------------
+template <class S, class R, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY) k_batch_step(const BatchMeta* __restrict__ meta,
+                                                       const BatchInst<S>* __restrict__ insts) {
+  __shared__ FusedSmem<R, TX, TY> sm;
+  __shared__ DevParams sP;
+  const int ntiles = meta->ntiles;
+  const BatchTile* __restrict__ tiles = meta->tiles;
+  int have = -1;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const BatchTile tile = tiles[t];
+    __syncthreads();  // the previous tile is done with the shared memory
+    if (tile.inst != have) {
+      const int* src = (const int*)&insts[tile.inst].P;
+      int* dst = (int*)&sP;
+      for (int k = threadIdx.x; k < (int)(sizeof(DevParams) / sizeof(int)); k += TX * TY) dst[k] = src[k];
+      have = tile.inst;
+      __syncthreads();
+    }
+    const BatchInst<S>& I = insts[tile.inst];
+    const int cur = I.cur;
+    const long long step = I.step;
+    const bool interior = tile.x0 >= 3 && tile.x0 + TX + 3 <= sP.nx && tile.y0 >= 3 && tile.y0 + TY + 3 <= sP.ny;
+    if (interior)
+      fused_body<true, S, R, TX, TY>(I.f[cur], I.g[cur], I.f[cur ^ 1], I.g[cur ^ 1], (R*)I.phi_prev, sP, step,
+                                     step == 0, I.scalars, I.partials, I.status, sm, tile.x0, tile.y0, tile.pslot);
+    else
+      fused_body<false, S, R, TX, TY>(I.f[cur], I.g[cur], I.f[cur ^ 1], I.g[cur ^ 1], (R*)I.phi_prev, sP, step,
+                                      step == 0, I.scalars, I.partials, I.status, sm, tile.x0, tile.y0, tile.pslot);
+  }
+}
+
+// One block per instance slot: rho_ave from the tile partials (fixed order), then flip the buffers
+// and count the step.
+template <class S>
+__global__ void __launch_bounds__(128) k_batch_advance(BatchInst<S>* __restrict__ insts) {
+  __shared__ double red[4];
+  BatchInst<S>& I = insts[blockIdx.x];
+  if (!I.active) return;
+  if (I.P.buoyancy) {
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < I.ntiles; j += 128) acc += I.partials[j];
+    acc = block_sum<128>(acc, red);
+    if (threadIdx.x == 0) I.scalars[0] = acc / (double)I.P.N;
+  }
+  if (threadIdx.x == 0) {
+    I.cur ^= 1;
+    I.step += 1;
+  }
+}
+
+template <class S, class R, int TX, int TY>
+static cudaError_t batch_launch_t(int ctas, const BatchMeta* d_meta, void* d_insts, int ninst, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  k_batch_step<S, R, TX, TY><<<sms * ctas, TX * TY, 0, st>>>(d_meta, (const BatchInst<S>*)d_insts);
+  if (ninst > 0) k_batch_advance<S><<<ninst, 128, 0, st>>>((BatchInst<S>*)d_insts);
+  return cudaGetLastError();
+}
+
+template <class S, class R>
+static cudaError_t batch_launch_p(int variant, int ctas, const BatchMeta* d_meta, void* d_insts, int ninst,
+                                  cudaStream_t st) {
+  if (variant == 1) return batch_launch_t<S, R, 32, 16>(ctas, d_meta, d_insts, ninst, st);
+  if (variant == 2) return batch_launch_t<S, R, 64, 8>(ctas, d_meta, d_insts, ninst, st);
+  return batch_launch_t<S, R, 32, 8>(ctas, d_meta, d_insts, ninst, st);
+}
+
+cudaError_t batch_step_launch(int prec, int variant, int ctas, const BatchMeta* d_meta, void* d_insts, int ninst,
+                              cudaStream_t st) {
+  if (prec == 0) return batch_launch_p<double, double>(variant, ctas, d_meta, d_insts, ninst, st);
+  if (prec == 1) return batch_launch_p<float, float>(variant, ctas, d_meta, d_insts, ninst, st);
+  return batch_launch_p<__half, float>(variant, ctas, d_meta, d_insts, ninst, st);
+}
+
+template <class S, class R, int TX, int TY> static int occ_t() {
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_step<S, R, TX, TY>, TX * TY, 0);
+  return n;
+}
+
+template <class S, class R> static int occ_p(int variant) {
+  if (variant == 1) return occ_t<S, R, 32, 16>();
+  if (variant == 2) return occ_t<S, R, 64, 8>();
+  return occ_t<S, R, 32, 8>();
+}
+
+int batch_max_ctas_per_sm(int prec, int variant) {
+  if (prec == 0) return occ_p<double, double>(variant);
+  if (prec == 1) return occ_p<float, float>(variant);
+  return occ_p<__half, float>(variant);
 }
 
 }  // namespace lbpc

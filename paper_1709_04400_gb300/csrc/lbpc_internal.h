@@ -36,6 +36,41 @@ cudaError_t split_export_pops(const SplitBuffers& b, const DevParams& P, int pre
 int split_nplanes();
 int split_block();
 
+// ---- batched step (lbpc_fused.cu kernels, lbpc_batch.cu host) ----
+// One instance of a batch as the device sees it; S is the storage type of the batch.
+template <class S> struct BatchInst {
+  DevParams P;
+  PopBuf<S> f[2], g[2];
+  void* phi_prev;      // arithmetic type
+  double* scalars;     // [0] rho_ave, [1] mass, [2] heat
+  double* partials;    // per-tile partial sums of rho (buoyancy) and per-block sums
+  long long* status;   // first non-physical node of this instance
+  long long step;      // steps taken
+  int cur;             // buffer holding the current state
+  int active;
+  int ntiles;          // tiles of this instance in the current work list
+  int pad_;
+};
+struct BatchTile {
+  int inst, x0, y0, pslot;
+};
+struct BatchMeta {
+  const BatchTile* tiles;
+  int ntiles;
+  int ninst;  // instance slots (active or not)
+};
+// Tile shapes a batch can run with: 0 = 32x8, 1 = 32x16, 2 = 64x8.
+constexpr int kBatchVariants = 3;
+inline void batch_tile_shape(int v, int& tx, int& ty) {
+  tx = v == 2 ? 64 : 32;
+  ty = v == 1 ? 16 : 8;
+}
+// Enqueue one batched step (persistent step kernel + per-instance advance) on st.
+cudaError_t batch_step_launch(int prec, int variant, int ctas, const BatchMeta* d_meta, void* d_insts, int ninst,
+                              cudaStream_t st);
+// Largest resident CTAs per SM of the step kernel for (prec, variant).
+int batch_max_ctas_per_sm(int prec, int variant);
+
 // Fused single-kernel step (lbpc_fused.cu); same buffers, no scratch planes touched.
 cudaError_t fused_step(const SplitBuffers& b, const DevParams& P, int prec, int cur, long long step, cudaStream_t st,
                        cudaEvent_t* ev = nullptr);

@@ -29,7 +29,10 @@ PATH_AUTO, PATH_SPLIT, PATH_FUSED = 0, 1, 2
 EXPORTED = ["lbpc_version", "lbpc_check_params", "lbpc_workspace_bytes", "lbpc_eos_critical", "lbpc_coexistence",
             "lbpc_create", "lbpc_init", "lbpc_step", "lbpc_step_async", "lbpc_check", "lbpc_fields", "lbpc_sums",
             "lbpc_populations", "lbpc_step_count", "lbpc_last_error", "lbpc_destroy", "lbpc_step_timed",
-            "lbpc_kernel_name", "lbpc_set_path", "lbpc_step_static"]
+            "lbpc_kernel_name", "lbpc_set_path", "lbpc_step_static", "lbpc_batch_instance_bytes", "lbpc_batch_create",
+            "lbpc_batch_add", "lbpc_batch_remove", "lbpc_batch_step", "lbpc_batch_check", "lbpc_batch_fields",
+            "lbpc_batch_sums", "lbpc_batch_step_count", "lbpc_batch_set_config", "lbpc_batch_config",
+            "lbpc_batch_autotune", "lbpc_batch_free_bytes", "lbpc_batch_last_error", "lbpc_batch_destroy"]
 
 
 class LbpcError(RuntimeError):
@@ -90,6 +93,22 @@ def load_library(path: str = LIB_PATH):
         "lbpc_kernel_name": (ctypes.c_char_p, [vp, ctypes.c_int32]),
         "lbpc_set_path": (ctypes.c_int, [vp, ctypes.c_int32]),
         "lbpc_step_static": (ctypes.c_int, [P, vp, vp, vp, vp, vp, vp, ctypes.c_int64, vp]),
+        "lbpc_batch_instance_bytes": (ctypes.c_size_t, [P]),
+        "lbpc_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]),
+        "lbpc_batch_add": (ctypes.c_int, [vp, P, vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int32)]),
+        "lbpc_batch_remove": (ctypes.c_int, [vp, ctypes.c_int32]),
+        "lbpc_batch_step": (ctypes.c_int, [vp, ctypes.c_int64]),
+        "lbpc_batch_check": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32)]),
+        "lbpc_batch_fields": (ctypes.c_int, [vp, ctypes.c_int32, vp, vp, vp, vp, ctypes.c_int]),
+        "lbpc_batch_sums": (ctypes.c_int, [vp, ctypes.c_int32, dp, dp]),
+        "lbpc_batch_step_count": (ctypes.c_int64, [vp, ctypes.c_int32]),
+        "lbpc_batch_set_config": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.c_int32]),
+        "lbpc_batch_config": (ctypes.c_int, [vp] + [ctypes.POINTER(ctypes.c_int32)] * 4),
+        "lbpc_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                               ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]),
+        "lbpc_batch_free_bytes": (ctypes.c_size_t, [vp]),
+        "lbpc_batch_last_error": (ctypes.c_char_p, [vp]),
+        "lbpc_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -324,3 +343,108 @@ def params_from_case(case: dict, prec: int = FP64) -> Params:
         flow_bc=[_FLOW[k] for k in case["flow_bc"]], rho_bc=case.get("rho_bc", (0.0,) * 4),
         t_bc=[_TBC[k] for k in case["t_bc"]], T_bc=case.get("T_bc", (0.0,) * 4), strip=case.get("strip"),
         G_wall=case.get("G_wall", 0.0))
+
+
+class Batch:
+    """Many simulations advancing together (lbpc_batch_*): one persistent launch per step over a
+    device work list of every instance's tiles, replayed through CUDA graphs on a dedicated stream.
+    The arena is a PyTorch uint8 buffer of arena_bytes."""
+
+    def __init__(self, prec: int, arena_bytes: int, max_instances: int = 4096, device=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("liblbpc needs a CUDA device; none is available")
+        self.lib = load_library()
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.prec = prec
+        with torch.cuda.device(self.device):
+            self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=self.device)
+            self.stream = torch.cuda.Stream(self.device)
+        h = ctypes.c_void_p()
+        s = self.lib.lbpc_batch_create(prec, max_instances, ctypes.c_void_p(self.arena.data_ptr()), int(arena_bytes),
+                                       ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if s != LBPC_OK:
+            raise LbpcError(s, "lbpc_batch_create")
+        self.h = h
+        self.shapes = {}
+
+    def _raise(self, s, what):
+        if s != LBPC_OK:
+            raise LbpcError(s, f"{what}: {self.lib.lbpc_batch_last_error(self.h).decode()}")
+
+    @staticmethod
+    def instance_bytes(params: Params) -> int:
+        c = params.to_c()
+        return int(load_library().lbpc_batch_instance_bytes(ctypes.byref(c)))
+
+    def add(self, params: Params, rho, T) -> int:
+        c = params.to_c()
+        rho = np.ascontiguousarray(np.asarray(rho, dtype=np.float64).reshape(params.ny, params.nx))
+        T = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(params.ny, params.nx))
+        i = ctypes.c_int32()
+        self._raise(self.lib.lbpc_batch_add(self.h, ctypes.byref(c), _ptr(rho), _ptr(T), 0, ctypes.byref(i)),
+                    "lbpc_batch_add")
+        self.shapes[i.value] = (params.ny, params.nx)
+        return i.value
+
+    def remove(self, i: int):
+        self._raise(self.lib.lbpc_batch_remove(self.h, int(i)), "lbpc_batch_remove")
+        self.shapes.pop(i, None)
+
+    def step(self, n: int = 1):
+        self._raise(self.lib.lbpc_batch_step(self.h, int(n)), "lbpc_batch_step")
+
+    def check(self):
+        f = ctypes.c_int32()
+        s = self.lib.lbpc_batch_check(self.h, ctypes.byref(f))
+        if s != LBPC_OK:
+            err = LbpcError(s, self.lib.lbpc_batch_last_error(self.h).decode())
+            err.instance = f.value
+            raise err
+
+    def fields(self, i: int):
+        ny, nx = self.shapes[i]
+        out = [np.empty((ny, nx)) for _ in range(4)]
+        self._raise(self.lib.lbpc_batch_fields(self.h, int(i), *[_ptr(a) for a in out], 0), "lbpc_batch_fields")
+        return tuple(out)
+
+    def sums(self, i: int):
+        m, h = ctypes.c_double(), ctypes.c_double()
+        self._raise(self.lib.lbpc_batch_sums(self.h, int(i), ctypes.byref(m), ctypes.byref(h)), "lbpc_batch_sums")
+        return m.value, h.value
+
+    def step_count(self, i: int) -> int:
+        return int(self.lib.lbpc_batch_step_count(self.h, int(i)))
+
+    def set_config(self, variant: int, ctas_per_sm: int):
+        self._raise(self.lib.lbpc_batch_set_config(self.h, int(variant), int(ctas_per_sm)), "lbpc_batch_set_config")
+
+    def config(self):
+        v = [ctypes.c_int32() for _ in range(4)]
+        self._raise(self.lib.lbpc_batch_config(self.h, *[ctypes.byref(x) for x in v]), "lbpc_batch_config")
+        return dict(tile_x=v[0].value, tile_y=v[1].value, ctas_per_sm=v[2].value, graph_chunk=v[3].value)
+
+    def autotune(self, steps_per_candidate: int = 4):
+        bv, bc, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+        self._raise(self.lib.lbpc_batch_autotune(self.h, int(steps_per_candidate), ctypes.byref(bv), ctypes.byref(bc),
+                                                 ctypes.byref(ms)), "lbpc_batch_autotune")
+        return dict(variant=bv.value, ctas_per_sm=bc.value, ms_per_step=ms.value)
+
+    def free_bytes(self) -> int:
+        return int(self.lib.lbpc_batch_free_bytes(self.h))
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            self.stream.synchronize()
+            self.lib.lbpc_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -74,3 +74,17 @@ def mixed_small(Tc, rho_v, rho_l, nx=37, ny=29, seed=inputs.SEED_BASE + 5):
                 t_bc=("none", "none", "dirichlet", "dirichlet"), T_bc=(0.0, 0.0, Ts, Ts),
                 strip=(nx // 4, nx // 2 + 1, Ts + 0.1 * Tc), G_wall=-0.2)
     return case, rho, T
+
+
+def batched_evaporation(Tc, rho_v, rho_l, count=256, side_lo=64, side_hi=512, seed=inputs.SEED_BASE + 3):
+    """Droplet-evaporation instances of uneven size: side uniform in {side_lo..side_hi}, radius
+    uniform in [0.15, 0.3] of the side, superheat uniform in [0.05, 0.3] T_c (seeded)."""
+    u = inputs.uniform(seed, 3 * count).reshape(count, 3)
+    out = []
+    for k in range(count):
+        n = side_lo + int(u[k, 0] * (side_hi - side_lo + 1))
+        radius = (0.15 + 0.15 * u[k, 1]) * n
+        dT = 0.05 + 0.25 * u[k, 2]
+        case, rho, T = droplet_evaporation(Tc, rho_v, rho_l, n=n, radius=radius, dT_ratio=dT)
+        out.append((case, rho, T))
+    return out

@@ -1,0 +1,159 @@
+"""Batched step (lbpc_batch_*): many instances of uneven size in one persistent launch per step.
+
+An instance's result must not depend on what else is in the batch: each one is checked bit for bit
+against the same instance in a batch of its own, and to round-off against the single-instance entry
+point (lbpc_create / lbpc_step, fused path). The oracle bounds the FP32 batch to 1e-4 and the FP64
+batch to 1e-10 as elsewhere."""
+
+import numpy as np
+import pytest
+
+from paper_1709_04400_gb300 import inputs, lbpc, workloads
+
+from .helpers import RL, RV, TC, TS, max_rel, norm_rel, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+
+    from paper_1709_04400_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def _cases():
+    """Uneven sizes and every boundary class."""
+    out = []
+    out.append(workloads.mixed_small(TC, RV, RL, nx=37, ny=29))
+    out.append(workloads.droplet_periodic(TC, RV, RL, n=64, radius=14.0))
+    out.append(workloads.droplet_evaporation(TC, RV, RL, n=96, radius=20.0, dT_ratio=0.2))
+    out.append(workloads.heated_wall(TC, RV, RL, nx=70, ny=90, strip_width=8))
+    out.append(workloads.mixed_small(TC, RV, RL, nx=33, ny=17))
+    return out
+
+
+def _alone(case, rho, T, steps, prec):
+    sim = lbpc.Simulation(lbpc.params_from_case(case, prec))
+    sim.set_path(lbpc.PATH_FUSED)
+    sim.init(rho, T)
+    sim.step(steps)
+    out = sim.fields()
+    sim.close()
+    return out
+
+
+def _solo(case, rho, T, steps, prec):
+    """The instance in a batch of its own (default configuration)."""
+    b = lbpc.Batch(prec, _arena_for([(case, rho, T)], prec))
+    i = b.add(lbpc.params_from_case(case, prec), rho, T)
+    b.step(steps)
+    out = b.fields(i)
+    b.close()
+    return out
+
+
+def _arena_for(cases, prec, extra=64 << 20):
+    return sum(lbpc.Batch.instance_bytes(lbpc.params_from_case(c, prec)) for c, _, _ in cases) + extra
+
+
+TOL_VS_SINGLE = {lbpc.FP32: 1e-5, lbpc.FP16DEV: 2e-3, lbpc.FP64: 1e-13}
+
+
+@pytest.mark.parametrize("prec", [lbpc.FP32, lbpc.FP16DEV, lbpc.FP64], ids=["fp32", "fp16", "fp64"])
+def test_batch_equals_alone(prec):
+    """Each instance of a mixed batch equals, bit for bit, the same instance in a batch of its own; and
+    it matches the single-instance entry point (a different tile shape of the same arithmetic, where
+    the compiler may contract multiply-adds differently) to a round-off tolerance."""
+    cases = _cases()
+    steps = 40  # two graph chunks of 16 plus 8 direct launches
+    b = lbpc.Batch(prec, _arena_for(cases, prec))
+    ids = [b.add(lbpc.params_from_case(c, prec), r, t) for c, r, t in cases]
+    b.step(steps)
+    b.check()
+    for i, (c, r, t) in zip(ids, cases):
+        got = b.fields(i)
+        assert b.step_count(i) == steps
+        solo = lbpc.Batch(prec, _arena_for([(c, r, t)], prec))
+        j = solo.add(lbpc.params_from_case(c, prec), r, t)
+        solo.step(steps)
+        for a, e in zip(got, solo.fields(j)):
+            assert np.array_equal(a, e), c["name"]
+        solo.close()
+        ref = _alone(c, r, t, steps, prec)
+        tol = TOL_VS_SINGLE[prec]
+        assert max_rel(got[0], ref[0]) < tol and max_rel(got[3], ref[3]) < tol, c["name"]
+        assert norm_rel(got[1], ref[1]) < 100 * tol and norm_rel(got[2], ref[2]) < 100 * tol, c["name"]
+    b.close()
+
+
+def test_batch_fp32_and_fp64_against_oracle():
+    case, rho, T = workloads.mixed_small(TC, RV, RL, nx=37, ny=29)
+    p, s = run_oracle(case, rho, T, 60)
+    from oracle import model
+
+    r_o, ux_o, uy_o, T_o = model.fields(p, s)
+    for prec, tol in ((lbpc.FP32, 1e-4), (lbpc.FP64, 1e-10)):
+        b = lbpc.Batch(prec, _arena_for([(case, rho, T)], prec))
+        i = b.add(lbpc.params_from_case(case, prec), rho, T)
+        b.step(60)
+        r, ux, uy, TT = b.fields(i)
+        b.close()
+        assert max_rel(r, r_o) < tol and max_rel(TT, T_o) < tol
+        assert norm_rel(ux, ux_o) < tol and norm_rel(uy, uy_o) < tol
+
+
+def test_instances_join_and_leave():
+    """B joins after A has run 10 steps; A leaves after 20; B's result equals B run alone."""
+    prec = lbpc.FP32
+    (ca, ra, ta), (cb, rb, tb) = _cases()[1], _cases()[2]
+    b = lbpc.Batch(prec, _arena_for([(ca, ra, ta), (cb, rb, tb)], prec))
+    ia = b.add(lbpc.params_from_case(ca, prec), ra, ta)
+    b.step(10)
+    ib = b.add(lbpc.params_from_case(cb, prec), rb, tb)
+    b.step(10)
+    got_a = b.fields(ia)
+    b.remove(ia)
+    b.step(22)
+    got_b = b.fields(ib)
+    b.close()
+    for a, e in zip(got_a, _solo(ca, ra, ta, 20, prec)):
+        assert np.array_equal(a, e)
+    for a, e in zip(got_b, _solo(cb, rb, tb, 32, prec)):
+        assert np.array_equal(a, e)
+
+
+def test_autotune_keeps_results():
+    prec = lbpc.FP32
+    cases = _cases()[:3]
+    b = lbpc.Batch(prec, _arena_for(cases, prec))
+    ids = [b.add(lbpc.params_from_case(c, prec), r, t) for c, r, t in cases]
+    best = b.autotune(steps_per_candidate=2)
+    n = b.step_count(ids[0])
+    assert n > 0 and best["ms_per_step"] > 0
+    b.step(5)
+    for i, (c, r, t) in zip(ids, cases):
+        got, ref = b.fields(i), _solo(c, r, t, n + 5, prec)
+        assert max_rel(got[0], ref[0]) < 1e-5 and max_rel(got[3], ref[3]) < 1e-5
+    b.close()
+
+
+def test_arena_full_and_slot_reuse():
+    prec = lbpc.FP32
+    case, rho, T = workloads.droplet_periodic(TC, RV, RL, n=64, radius=14.0)
+    per = lbpc.Batch.instance_bytes(lbpc.params_from_case(case, prec))
+    b = lbpc.Batch(prec, 2 * per + (64 << 10), max_instances=8)  # room for the descriptors, not a third instance
+    i1 = b.add(lbpc.params_from_case(case, prec), rho, T)
+    i2 = b.add(lbpc.params_from_case(case, prec), rho, T)
+    with pytest.raises(lbpc.LbpcError) as e:
+        b.add(lbpc.params_from_case(case, prec), rho, T)
+    assert e.value.status == lbpc.LBPC_ENOMEM
+    b.remove(i1)
+    i3 = b.add(lbpc.params_from_case(case, prec), rho, T)
+    assert i3 == i1
+    b.step(3)
+    assert b.step_count(i3) == 3 and b.step_count(i2) == 3
+    b.close()
