@@ -35,7 +35,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="evaporation", choices=["evaporation", "droplet", "heated_wall", "batch"])
+    ap.add_argument("--workload", default="evaporation",
+                    choices=["evaporation", "droplet", "heated_wall", "batch", "serve"])
+    ap.add_argument("--requests", type=int, default=300, help="served workload: number of requests")
+    ap.add_argument("--rate", type=float, default=40.0, help="served workload: Poisson arrival rate (1/s)")
     ap.add_argument("--instances", type=int, default=256, help="batched workload: number of instances")
     ap.add_argument("--n", type=int, default=0, help="grid side (0 = the workload's own size)")
     ap.add_argument("--dT", type=float, default=0.1, help="superheat dT / T_c of the evaporation case")
@@ -406,6 +409,38 @@ def run_batch(args):
         print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """Served stream: Poisson arrivals of mixed evaporation / heated-wall requests, admitted by the
+    arena budget, advanced together by continuous batching; p50/p99 time-to-result and aggregate
+    MLUPS. A bounded sample of the 2000-request stream (smaller sides and step counts)."""
+    import torch
+
+    from paper_1709_04400_gb300 import build, lbpc, serve
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    build.build()
+    prec = {"": lbpc.FP32, "fp32": lbpc.FP32, "fp16": lbpc.FP16DEV, "fp64": lbpc.FP64}[args.prec]
+    reqs = serve.poisson_stream(args.requests, rate=args.rate, seed=170904400 + 4, side_lo=64, side_hi=512,
+                                steps_lo=1000, steps_hi=5000)
+    srv = serve.Server(prec=prec, hbm_budget_bytes=24 << 30)
+    with ClockSampler(local) as clk:
+        srv.run(reqs)
+    st = srv.stats()
+    srv.close()
+    if rank == 0:
+        line = {"metric": "served coupled flow+thermal MLUPS (aggregate)", "value": st["aggregate_mlups"],
+                "unit": "MLUPS", "n_gpus": 1, "steps": None, "warmup": 0, "ms_per_step": None,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if prec == lbpc.FP64 else "f32", "data": "synthetic",
+                "config": {"workload": f"served_stream_{args.requests}", "rate_per_s": args.rate,
+                           "sides": [64, 512], "steps": [1000, 5000], "mix": "half evaporation, half heated wall",
+                           "storage": args.prec or "fp32", "budget_gb": 24},
+                "latency": {"p50_s": st["p50_s"], "p99_s": st["p99_s"], "mean_s": st["mean_s"]},
+                "served": st, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
@@ -448,5 +483,7 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.workload == "batch":
         run_batch(a)
+    elif a.workload == "serve":
+        run_serve(a)
     else:
         run_native(a)

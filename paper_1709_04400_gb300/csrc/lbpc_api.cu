@@ -27,6 +27,7 @@ struct lbpc_ctx {
   size_t stage_bytes;   // bytes of one A/B half (f and g): the FP64 staging room between steps
   long long step;
   int initialised;
+  lbpc::TmaMaps tma[2];  // tensor maps of buffers A and B (TMA-staged fused step)
   cudaEvent_t ev[8];    // created on first lbpc_step_timed
   int have_events;
   lbpc_status err;
@@ -325,8 +326,9 @@ LBPC_API lbpc_status lbpc_create(const lbpc_params* p, void* ws, size_t bytes, v
   if (!ws) return LBPC_EINVAL;
   if (((uintptr_t)ws & 255) != 0) return LBPC_EINVAL;
   if (bytes < L.total) return LBPC_ENOMEM;
-  lbpc_ctx* c = (lbpc_ctx*)calloc(1, sizeof(lbpc_ctx));
+  lbpc_ctx* c = (lbpc_ctx*)aligned_alloc(64, (sizeof(lbpc_ctx) + 63) / 64 * 64);
   if (!c) return LBPC_ENOMEM;
+  memset(c, 0, sizeof(lbpc_ctx));
   c->p = *p;
   c->dp = make_dev_params(p);
   if (cudaGetDevice(&c->device) != cudaSuccess) {
@@ -352,6 +354,9 @@ LBPC_API lbpc_status lbpc_create(const lbpc_params* p, void* ws, size_t bytes, v
   c->step = 0;
   c->err = LBPC_OK;
   c->msg[0] = 0;
+  for (int k = 0; k < 2; ++k)
+    if (lbpc::fused_tma_encode(&c->tma[k], p->prec, c->buf.f[k], c->buf.g[k], c->buf.ref_f[k], c->buf.ref_g[k], c->dp))
+      c->buf.tma[k] = &c->tma[k];
   *out = c;
   return LBPC_OK;
 }
@@ -433,11 +438,13 @@ static lbpc_status check_status(lbpc_ctx* c) {
   CU(c, cudaMemcpyAsync(st, c->buf.status, sizeof st, cudaMemcpyDeviceToHost, c->stream), "status D2H");
   CU(c, cudaStreamSynchronize(c->stream), "status sync");
   if (st[0] != 0) {
-    static const char* what[] = {"?", "rho <= 0", "rho >= 1/b (EOS pole)", "T <= 0", "psi^2 < 0", "non-finite value"};
+    static const char* what[] = {"?", "rho <= 0", "rho >= 1/b (EOS pole)", "T <= 0", "psi^2 < 0", "non-finite value",
+                                 "a bounded wait for a tile copy gave up"};
     char m[256];
-    snprintf(m, sizeof m, "non-physical state at step %lld, node (x=%lld, y=%lld): %s", st[1], st[2], st[3],
-             what[(st[4] >= 1 && st[4] <= 5) ? st[4] : 0]);
-    return fail(c, LBPC_ENONPHYS, m);
+    snprintf(m, sizeof m, "%s at step %lld, node (x=%lld, y=%lld): %s",
+             st[4] == lbpc::ST_TIMEOUT ? "device timeout" : "non-physical state", st[1], st[2], st[3],
+             what[(st[4] >= 1 && st[4] <= 6) ? st[4] : 0]);
+    return fail(c, st[4] == lbpc::ST_TIMEOUT ? LBPC_ETIMEOUT : LBPC_ENONPHYS, m);
   }
   return LBPC_OK;
 }

@@ -14,7 +14,7 @@
 namespace lbpc {
 
 enum { BC_PERIODIC = 0, BC_WALL = 1, BC_PRESSURE = 2 };
-enum { ST_RHO_LE0 = 1, ST_RHO_POLE = 2, ST_T_LE0 = 3, ST_PSI2_NEG = 4, ST_NONFINITE = 5 };
+enum { ST_RHO_LE0 = 1, ST_RHO_POLE = 2, ST_T_LE0 = 3, ST_PSI2_NEG = 4, ST_NONFINITE = 5, ST_TIMEOUT = 6 };
 
 __host__ __device__ constexpr int EX(int a) { return a == 1 || a == 5 || a == 8 ? 1 : (a == 3 || a == 6 || a == 7 ? -1 : 0); }
 __host__ __device__ constexpr int EY(int a) { return a == 2 || a == 5 || a == 6 ? 1 : (a == 4 || a == 7 || a == 8 ? -1 : 0); }

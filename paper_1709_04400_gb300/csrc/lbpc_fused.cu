@@ -11,6 +11,9 @@
 // HBM sees the populations read once and written once plus phi (the algorithmic 152 B/node in FP32);
 // the ring re-reads of neighbouring tiles' populations are served by L2. Ghost rows beyond a
 // non-periodic y edge copy the edge row (moments, psi and, through the clamped stencil, F and v).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "lbpc_device.cuh"
 #include "lbpc_internal.h"
 
@@ -40,6 +43,77 @@ __device__ __forceinline__ int row_of(const DevParams& P, int y) {
 
 }  // namespace
 
+// ------------------------------------------------------------------------------------------------
+// TMA staging of an interior tile: every population plane's box of the tile plus its pull halo is
+// copied to shared memory by the tensor-memory accelerator, so the pulls become shared-memory reads.
+// Box: BY = TY + 6 rows from y0 - 3, BX columns from x0 - XOFF (XOFF keeps the start 16-byte aligned).
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: about a second of polling at most; false if the phase did not complete.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  for (unsigned it = 0; it < (1u << 20); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          smem_u32(dst)),
+      "l"(tm), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(tm), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory view of a staged tile.
+template <class S> struct TmaTile {
+  const unsigned char* base;  // 18 population planes (f then g), then the f and g reference planes
+};
+
+template <class S, class R, int TX, int TY>
+__device__ __forceinline__ void pull_staged(const TmaTile<S>& t, int set, const R* w, int hx, int hy, R v[9]) {
+  using B = TmaBox<S, TX, TY>;
+  const S* pop = (const S*)(t.base + (size_t)set * 9 * B::PLANE);
+  const float* ref = (const float*)(t.base + 18 * B::PLANE + (size_t)set * B::RPLANE);
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    const int row = hy + 1 - EY(a), col = hx + B::XOFF - 2 - EX(a);
+    const S* pa = (const S*)((const unsigned char*)pop + a * B::PLANE);
+    if constexpr (B::HALF) {
+      v[a] = R(__half2float(pa[row * B::BX + col])) + w[a] * R(ref[row * B::REFX + col]);
+    } else {
+      v[a] = R(pa[row * B::BX + col]);
+    }
+  }
+}
+
 template <class R, int TX, int TY> struct FusedSmem {
   R rho[TY + 4][TX + 4], T[TY + 4][TX + 4], psi[TY + 4][TX + 4], jx[TY + 4][TX + 4], jy[TY + 4][TX + 4];
   R vx[TY + 2][TX + 2], vy[TY + 2][TX + 2];
@@ -48,13 +122,14 @@ template <class R, int TX, int TY> struct FusedSmem {
 
 // INTERIOR: the tile, its 2-ring and their pull sources lie inside the domain away from every edge,
 // so no index wraps, no boundary closure applies and no ghost row exists (a per-CTA, uniform choice).
-template <bool INTERIOR, class S, class R, int TX, int TY>
+template <int MODE, class S, class R, int TX, int TY>
 __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S>& gsrc, const PopBuf<S>& fdst,
                                            const PopBuf<S>& gdst, R* __restrict__ phi_prev,
                                            const DevParams& P, long long step, int first,
                                            const double* __restrict__ rho_ave, double* __restrict__ partials,
                                            long long* __restrict__ status, FusedSmem<R, TX, TY>& sm, int x0, int y0,
-                                           int pslot) {
+                                           int pslot, const TmaTile<S> staged = TmaTile<S>{nullptr}) {
+  constexpr bool INTERIOR = MODE != 0;
   constexpr int RX = TX + 4, RY = TY + 4;  // stage-1 region (tile + 2)
   constexpr int VX = TX + 2, VY = TY + 2;  // stage-2 region (tile + 1)
   (void)RY;
@@ -77,7 +152,10 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
 
   // ---- stage 1a: own node (kept in registers) ----
   R f[9], g[9];
-  if (INTERIOR) {
+  if (MODE == 2) {
+    pull_staged<S, R, TX, TY>(staged, 0, C.wf, tx + 2, ty + 2, f);
+    pull_staged<S, R, TX, TY>(staged, 1, C.wg, tx + 2, ty + 2, g);
+  } else if (INTERIOR) {
     const long long io = (long long)gy * P.nx + gx;
     pull_interior<S, R>(fsrc, C.wf, P.N, P.nx, io, f);
     pull_interior<S, R>(gsrc, C.wg, P.N, P.nx, io, g);
@@ -117,7 +195,10 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
       hx = c < 2 ? c : TX + c;
     }
     R fr[9], gr[9];
-    if (INTERIOR) {
+    if (MODE == 2) {
+      pull_staged<S, R, TX, TY>(staged, 0, C.wf, hx, hy, fr);
+      pull_staged<S, R, TX, TY>(staged, 1, C.wg, hx, hy, gr);
+    } else if (INTERIOR) {
       const long long io = (long long)(y0 + hy - 2) * P.nx + (x0 + hx - 2);
       pull_interior<S, R>(fsrc, C.wf, P.N, P.nx, io, fr);
       pull_interior<S, R>(gsrc, C.wg, P.N, P.nx, io, gr);
@@ -259,11 +340,53 @@ __global__ void __launch_bounds__(TX* TY) k_fused(PopBuf<S> fsrc, PopBuf<S> gsrc
   const bool interior = x0 >= 3 && x0 + TX + 3 <= P.nx && y0 >= 3 && y0 + TY + 3 <= P.ny;
   const int pslot = blockIdx.y * gridDim.x + blockIdx.x;
   if (interior)
-    fused_body<true, S, R, TX, TY>(fsrc, gsrc, fdst, gdst, phi_prev, P, step, first, rho_ave, partials, status, sm, x0,
-                                   y0, pslot);
+    fused_body<1, S, R, TX, TY>(fsrc, gsrc, fdst, gdst, phi_prev, P, step, first, rho_ave, partials, status, sm, x0, y0,
+                                pslot);
   else
-    fused_body<false, S, R, TX, TY>(fsrc, gsrc, fdst, gdst, phi_prev, P, step, first, rho_ave, partials, status, sm,
-                                    x0, y0, pslot);
+    fused_body<0, S, R, TX, TY>(fsrc, gsrc, fdst, gdst, phi_prev, P, step, first, rho_ave, partials, status, sm, x0, y0,
+                                pslot);
+}
+
+// Same step with the interior tiles' populations staged in shared memory by TMA (dynamic shared
+// memory of TmaBox<S, TX, TY>::BYTES). Tiles that touch an edge take the general path.
+template <class S, class R, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY) k_fused_tma(PopBuf<S> fsrc, PopBuf<S> gsrc, PopBuf<S> fdst, PopBuf<S> gdst,
+                                                       R* __restrict__ phi_prev, DevParams P, long long step, int first,
+                                                       const double* __restrict__ rho_ave,
+                                                       double* __restrict__ partials, long long* __restrict__ status,
+                                                       const __grid_constant__ TmaMaps maps) {
+  using B = TmaBox<S, TX, TY>;
+  __shared__ FusedSmem<R, TX, TY> sm;
+  extern __shared__ __align__(128) unsigned char dyn[];
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const bool interior = x0 >= 3 && x0 + TX + 3 <= P.nx && y0 >= 3 && y0 + TY + 3 <= P.ny;
+  const int pslot = blockIdx.y * gridDim.x + blockIdx.x;
+  if (!interior) {
+    fused_body<0, S, R, TX, TY>(fsrc, gsrc, fdst, gdst, phi_prev, P, step, first, rho_ave, partials, status, sm, x0, y0,
+                                pslot);
+    return;
+  }
+  uint64_t* bar = (uint64_t*)(dyn + B::BYTES - 128);
+  if (threadIdx.x == 0) mbar_init(bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(bar, (unsigned)(18 * B::BX * B::BY * sizeof(S) + (B::HALF ? 2 * B::REFX * B::BY * 4 : 0)));
+    for (int a = 0; a < 9; ++a) {
+      tma_load_3d(dyn + a * B::PLANE, &maps.f, x0 - B::XOFF, y0 - 3, a, bar);
+      tma_load_3d(dyn + (9 + a) * B::PLANE, &maps.g, x0 - B::XOFF, y0 - 3, a, bar);
+    }
+    if (B::HALF) {
+      tma_load_2d(dyn + 18 * B::PLANE, &maps.rf, x0 - B::XOFF, y0 - 3, bar);
+      tma_load_2d(dyn + 18 * B::PLANE + B::RPLANE, &maps.rg, x0 - B::XOFF, y0 - 3, bar);
+    }
+  }
+  if (!mbar_wait_bounded(bar, 0)) {
+    if (threadIdx.x == 0) report(status, step, x0, y0, ST_TIMEOUT);
+    mbar_wait_bounded(bar, 0);  // let the copies in flight land before the block's shared memory goes away
+    return;
+  }
+  fused_body<2, S, R, TX, TY>(fsrc, gsrc, fdst, gdst, phi_prev, P, step, first, rho_ave, partials, status, sm, x0, y0,
+                              pslot, TmaTile<S>{dyn});
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -271,11 +394,22 @@ template <class S, class R, int TX, int TY>
 static cudaError_t fused_impl(const SplitBuffers& b, const DevParams& P, int cur, long long step, cudaStream_t st,
                               cudaEvent_t* ev) {
   dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
+  const PopBuf<S> fs{(S*)b.f[cur], b.ref_f[cur]}, gs{(S*)b.g[cur], b.ref_g[cur]};
+  const PopBuf<S> fd{(S*)b.f[cur ^ 1], b.ref_f[cur ^ 1]}, gd{(S*)b.g[cur ^ 1], b.ref_g[cur ^ 1]};
   if (ev) cudaEventRecord(ev[0], st);
-  k_fused<S, R, TX, TY><<<grid, TX * TY, 0, st>>>(
-      PopBuf<S>{(S*)b.f[cur], b.ref_f[cur]}, PopBuf<S>{(S*)b.g[cur], b.ref_g[cur]},
-      PopBuf<S>{(S*)b.f[cur ^ 1], b.ref_f[cur ^ 1]}, PopBuf<S>{(S*)b.g[cur ^ 1], b.ref_g[cur ^ 1]}, (R*)b.phi_prev, P,
-      step, step == 0, b.scalars, b.partials, b.status);
+  if (b.tma[cur]) {
+    using B = TmaBox<S, TX, TY>;
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_fused_tma<S, R, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, B::BYTES);
+      attr = true;
+    }
+    k_fused_tma<S, R, TX, TY><<<grid, TX * TY, B::BYTES, st>>>(fs, gs, fd, gd, (R*)b.phi_prev, P, step, step == 0,
+                                                               b.scalars, b.partials, b.status, *b.tma[cur]);
+  } else {
+    k_fused<S, R, TX, TY><<<grid, TX * TY, 0, st>>>(fs, gs, fd, gd, (R*)b.phi_prev, P, step, step == 0, b.scalars,
+                                                    b.partials, b.status);
+  }
   if (ev) cudaEventRecord(ev[1], st);
   if (P.buoyancy) {
     fused_finish(b, P, (int)(grid.x * grid.y), st);
@@ -284,9 +418,65 @@ static cudaError_t fused_impl(const SplitBuffers& b, const DevParams& P, int cur
   return cudaGetLastError();
 }
 
+// ---- tensor maps of the TMA-staged path ----
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+template <class S, int TX, int TY>
+static bool encode_t(TmaMaps* m, void* f, void* g, float* rf, float* rg, const DevParams& P) {
+  using B = TmaBox<S, TX, TY>;
+  auto fn = encode_fn();
+  if (!fn) return false;
+  if (((size_t)P.nx * sizeof(S)) % 16 != 0) return false;  // row stride must be a multiple of 16 bytes
+  const CUtensorMapDataType dt = sizeof(S) == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                : (sizeof(S) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64);
+  const cuuint64_t dims[3] = {(cuuint64_t)P.nx, (cuuint64_t)P.ny, 9};
+  const cuuint64_t strides[2] = {(cuuint64_t)P.nx * sizeof(S), (cuuint64_t)P.N * sizeof(S)};
+  const cuuint32_t box[3] = {(cuuint32_t)B::BX, (cuuint32_t)B::BY, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  auto enc3 = [&](CUtensorMap* t, void* base) {
+    return fn(t, dt, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  if (!enc3(&m->f, f) || !enc3(&m->g, g)) return false;
+  if (B::HALF) {
+    const cuuint64_t d2[2] = {(cuuint64_t)P.nx, (cuuint64_t)P.ny};
+    const cuuint64_t s2[1] = {(cuuint64_t)P.nx * 4};
+    const cuuint32_t b2[2] = {(cuuint32_t)B::REFX, (cuuint32_t)B::BY};
+    auto enc2 = [&](CUtensorMap* t, void* base) {
+      return fn(t, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, d2, s2, b2, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+             CUDA_SUCCESS;
+    };
+    if (!enc2(&m->rf, rf) || !enc2(&m->rg, rg)) return false;
+  }
+  return true;
+}
+
+bool fused_tma_encode(TmaMaps* m, int prec, void* f, void* g, float* rf, float* rg, const DevParams& P) {
+  if (prec == 1) return encode_t<float, 32, 16>(m, f, g, rf, rg, P);
+  if (prec == 2) return encode_t<__half, 32, 16>(m, f, g, rf, rg, P);
+  return false;  // FP64 runs the split step by default; its fused form keeps per-thread loads
+}
+
 cudaError_t fused_step(const SplitBuffers& b, const DevParams& P, int prec, int cur, long long step, cudaStream_t st,
                        cudaEvent_t* ev) {
-  if (prec == 0) return fused_impl<double, double, 32, 8>(b, P, cur, step, st, ev);
+  if (prec == 0) {
+    SplitBuffers nb = b;
+    nb.tma[0] = nb.tma[1] = nullptr;
+    return fused_impl<double, double, 32, 8>(nb, P, cur, step, st, ev);
+  }
   if (prec == 1) return fused_impl<float, float, 32, 16>(b, P, cur, step, st, ev);
   return fused_impl<__half, float, 32, 16>(b, P, cur, step, st, ev);
 }

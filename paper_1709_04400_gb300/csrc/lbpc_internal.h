@@ -1,11 +1,29 @@
 // Internal interfaces between the C-ABI layer (lbpc_api.cu) and the kernel files.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "lbpc_device.cuh"
 
 namespace lbpc {
+
+template <class S, int TX, int TY> struct TmaBox {
+  static constexpr int XOFF = 16 / (int)sizeof(S) > 4 ? 16 / (int)sizeof(S) : 4;
+  static constexpr int EPR = 16 / (int)sizeof(S);                // elements per 16 bytes
+  static constexpr int BX = ((TX + XOFF + 3 + EPR - 1) / EPR) * EPR;
+  static constexpr int BY = TY + 6;
+  static constexpr int PLANE = ((BX * BY * (int)sizeof(S) + 127) / 128) * 128;  // bytes, 128-aligned
+  static constexpr int REFX = ((TX + XOFF + 3 + 3) / 4) * 4;                    // float reference planes
+  static constexpr int RPLANE = ((REFX * BY * 4 + 127) / 128) * 128;
+  static constexpr bool HALF = is_half_t<S>::value;
+  static constexpr int BYTES = 18 * PLANE + (HALF ? 2 * RPLANE : 0) + 128;       // + the mbarrier
+};
+
+struct alignas(64) TmaMaps {
+  CUtensorMap f, g, rf, rg;  // current buffer's populations (3D) and FP16 reference planes (2D)
+};
+
 
 // Device buffers of a context, carved from the caller's workspace.
 struct SplitBuffers {
@@ -18,6 +36,7 @@ struct SplitBuffers {
   double* partials;  // 2 * nblocks per-block partial sums
   double* scalars;   // [0] rho_ave, [1] mass, [2] heat
   long long* status; // [0] flag, [1] step, [2] x, [3] y, [4] code
+  const TmaMaps* tma[2] = {nullptr, nullptr};  // tensor maps of buffer A / B for the TMA-staged fused step
 };
 
 // ev: null, or split_kernel_count(P) + 1 events recorded before the first and after each kernel.
@@ -74,6 +93,9 @@ int batch_max_ctas_per_sm(int prec, int variant);
 // Fused single-kernel step (lbpc_fused.cu); same buffers, no scratch planes touched.
 cudaError_t fused_step(const SplitBuffers& b, const DevParams& P, int prec, int cur, long long step, cudaStream_t st,
                        cudaEvent_t* ev = nullptr);
+// Encode the tensor maps of one buffer (populations f, g and, for FP16, the reference planes) for the
+// TMA-staged fused step; false when the layout does not allow TMA (row stride not 16-byte aligned).
+bool fused_tma_encode(TmaMaps* m, int prec, void* f, void* g, float* rf, float* rg, const DevParams& P);
 // rho_ave <- sum of n per-tile partials / N (fixed order), on st.
 void fused_finish(const SplitBuffers& b, const DevParams& P, int n, cudaStream_t st);
 
