@@ -68,8 +68,11 @@ typedef enum { LBPC_T_NONE = 0, LBPC_T_DIRICHLET = 1 } lbpc_thermal_bc;
 typedef enum { LBPC_LAMBDA_CONST = 0, LBPC_LAMBDA_RHO_CV_CHI = 1 } lbpc_lambda_mode;
 
 /* LBPC_IMPROVED: the paper's model (Eq. 53 equilibria, S0 = phi + 0.5 dt d_t phi, Eqs. 54-55).
- * LBPC_COMPROMISED: the comparison model of Sec. IV (Eq. 44 equilibria, S0 = phi, no corrections). */
-typedef enum { LBPC_IMPROVED = 0, LBPC_COMPROMISED = 1 } lbpc_thermal_model;
+ * LBPC_COMPROMISED: the comparison model of Sec. IV (Eq. 44 equilibria, S0 = phi, no corrections).
+ * LBPC_GONG_CHENG: the model the paper improves on (Eqs. 11-14): BGK with the second-order
+ * equilibrium of Eq. 14, tau_g = lambda/(rho c_s^2 c_V) + 1/2 (Sec. IV A) and the source w_a phi of
+ * Eq. 13; s_g is not used. */
+typedef enum { LBPC_IMPROVED = 0, LBPC_COMPROMISED = 1, LBPC_GONG_CHENG = 2 } lbpc_thermal_model;
 
 /* Edge order in the arrays below: 0 = x-, 1 = x+, 2 = y- (bottom, y = 0), 3 = y+ (top, y = ny-1). */
 typedef struct {

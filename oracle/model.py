@@ -80,7 +80,7 @@ class OracleParams:
     T_bc: Tuple[float, float, float, float] = (0.0,) * 4
     strip: Optional[Tuple[int, int, float]] = None  # heated strip on the y- row: [x0, x1) at T
     G_wall: float = 0.0
-    model: str = "improved"  # improved | compromised
+    model: str = "improved"  # improved | compromised | gong_cheng
     frozen_flow: Optional[Tuple[float, float]] = None
     frozen_thermal: bool = False
 
@@ -91,7 +91,7 @@ class OracleParams:
             raise ValueError("y edges must be both periodic or both non-periodic")
         if self.strip is not None and self.t_bc[2] != "dirichlet":
             raise ValueError("a heated strip needs a Dirichlet y- edge")
-        if self.model not in ("improved", "compromised"):
+        if self.model not in ("improved", "compromised", "gong_cheng"):
             raise ValueError(self.model)
 
 
@@ -122,8 +122,12 @@ def flow_meq(rho, vx, vy):
 
 def heat_meq(T, vx, vy, model):
     """Thermal equilibrium moments: Eq. 53, T(1,-2,2,vx,-vx,vy,-vy,0,0), for the improved model;
-    Eq. 44, T(1,-2,1,vx,-vx,vy,-vy,0,0), for the compromised model (READING, Sec. IV)."""
+    Eq. 44, T(1,-2,1,vx,-vx,vy,-vy,0,0), for the compromised model (READING, Sec. IV); for the
+    Gong-Cheng model the moments of Eq. 14, w T [1 + e.v/c_s^2 + vv:(ee - c_s^2 I)/(2 c_s^4)], which
+    are those of the second-order equilibrium with rho replaced by T."""
     z = np.zeros_like(T)
+    if model == "gong_cheng":
+        return flow_meq(T, vx, vy)
     m2 = 2.0 * T if model == "improved" else T
     return np.stack([T, -2.0 * T, m2, T * vx, -T * vx, T * vy, -T * vy, z, z])
 
@@ -248,10 +252,18 @@ def macroscopic(p: OracleParams, s: OracleState):
     else:  # lambda = rho c_V chi: div(lambda grad T) = lambda lap T + grad lambda . grad T (Sec. IV A)
         grx, gry = grad(rho, p)
         div_lam_gradT = rcv * p.chi * lapT + p.cV * p.chi * (grx * gTx + gry * gTy)
-    k = (1.0 / p.s_g[3] - 0.5) * L.CS2
-    phi = div_lam_gradT / rcv - k * lapT + T * (1.0 - dpdT / rcv) * divv
+    if p.model == "gong_cheng":
+        # Eq. 13: the Gong-Cheng source keeps only the compression term; conduction is left to the
+        # LB diffusivity chi = (tau_g - 1/2) c_s^2 with tau_g = lambda/(rho c_s^2 c_V) + 1/2 (Sec. IV A)
+        phi = T * (1.0 - dpdT / rcv) * divv
+        lam = p.lam if p.lambda_mode == "const" else rcv * p.chi
+        tau_g = lam / (rho * L.CS2 * p.cV) + 0.5
+    else:
+        k = (1.0 / p.s_g[3] - 0.5) * L.CS2
+        phi = div_lam_gradT / rcv - k * lapT + T * (1.0 - dpdT / rcv) * divv
+        tau_g = None
     return dict(rho=rho, jx=jx, jy=jy, T=T, p=pe, dpdT=dpdT, psi=psi, Fx=Fx, Fy=Fy, Fix=Fix, Fiy=Fiy,
-                vx=vx, vy=vy, gTx=gTx, gTy=gTy, lapT=lapT, divv=divv, phi=phi)
+                vx=vx, vy=vy, gTx=gTx, gTy=gTy, lapT=lapT, divv=divv, phi=phi, tau_g=tau_g)
 
 
 def collide_flow(p: OracleParams, f, mac):
@@ -278,11 +290,16 @@ def collide_heat(p: OracleParams, g, mac, S0):
 
     m* = m - Lambda (m - m_eq) + (S0, 0, ..., 0);
     m3* += (1 - s3/2) s4 m4^(1),  m5* += (1 - s5/2) s6 m6^(1),  with dt m^(1) ~ m - m_eq (dt = 1).
-    The compromised model (Sec. IV) omits both corrections.
+    The compromised model (Sec. IV) omits both corrections; the Gong-Cheng model (Eqs. 12-14) is BGK.
     """
     T, vx, vy = mac["T"], mac["vx"], mac["vy"]
     m = L.to_moments(g)
     meq = heat_meq(T, vx, vy, p.model)
+    if p.model == "gong_cheng":
+        # Eq. 12: BGK with the local tau_g, source G_a = w_a phi (moments phi (1, -2, 1, 0, ..., 0))
+        G = np.zeros_like(m)
+        G[0], G[1], G[2] = S0, -2.0 * S0, S0
+        return L.from_moments(m - (m - meq) / mac["tau_g"] + G)
     s = np.asarray(p.s_g, dtype=np.float64)
     mstar = m - s[:, None, None] * (m - meq)
     mstar[0] = mstar[0] + S0

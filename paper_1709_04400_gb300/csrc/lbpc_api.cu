@@ -232,7 +232,8 @@ LBPC_API lbpc_status lbpc_check_params(const lbpc_params* p, char* msg, size_t n
   if (p->nx < 2 || p->ny < 2) BAD("grid %d x %d: nx and ny must be >= 2", p->nx, p->ny);
   if ((long long)p->nx * p->ny > (1ll << 31)) BAD("grid %d x %d exceeds 2^31 nodes", p->nx, p->ny);
   if (p->prec != LBPC_FP64 && p->prec != LBPC_FP32 && p->prec != LBPC_FP16DEV) BAD("prec %d unknown", p->prec);
-  if (p->model != LBPC_IMPROVED && p->model != LBPC_COMPROMISED) BAD("model %d unknown", p->model);
+  if (p->model != LBPC_IMPROVED && p->model != LBPC_COMPROMISED && p->model != LBPC_GONG_CHENG)
+    BAD("model %d unknown", p->model);
   if (p->lambda_mode != LBPC_LAMBDA_CONST && p->lambda_mode != LBPC_LAMBDA_RHO_CV_CHI) BAD("lambda_mode %d unknown", p->lambda_mode);
   if (p->flow_bc[0] != LBPC_PERIODIC || p->flow_bc[1] != LBPC_PERIODIC) BAD("x edges must be periodic");
   for (int k = 2; k < 4; ++k)

@@ -223,8 +223,22 @@ template <class R> __device__ __forceinline__ void flow_closure(R f[9], const De
   }
 }
 
-// Thermal equilibrium moments (Eq. 53 for the improved model, Eq. 44 for the compromised one).
+// Thermal equilibrium moments (Eq. 53 for the improved model, Eq. 44 for the compromised one, and for
+// the Gong-Cheng model the moments of Eq. 14: the second-order equilibrium with rho replaced by T).
 template <class R> __device__ __forceinline__ void heat_meq(R T, R vx, R vy, int model, R n[9]) {
+  if (model == 2) {
+    const R v2 = vx * vx + vy * vy;
+    n[0] = T;
+    n[1] = T * (R(-2) + R(3) * v2);
+    n[2] = T * (R(1) - R(3) * v2);
+    n[3] = T * vx;
+    n[4] = -T * vx;
+    n[5] = T * vy;
+    n[6] = -T * vy;
+    n[7] = T * (vx * vx - vy * vy);
+    n[8] = T * vx * vy;
+    return;
+  }
   n[0] = T;
   n[1] = R(-2) * T;
   n[2] = model == 0 ? R(2) * T : T;
@@ -328,10 +342,22 @@ __device__ __forceinline__ void collide_flow(R f[9], R rho, R vx, R vy, R Fx, R 
 
 // Thermal MRT collision of the improved model: Eq. 45 with m_eq of Eq. 53 and S = (S0, 0, ..., 0)
 // (Eq. 46), then m3* += (1 - s3/2) s4 (m4 - m4_eq) and m5* += (1 - s5/2) s6 (m6 - m6_eq) (Eqs. 54-55).
-template <class R> __device__ __forceinline__ void collide_heat(R g[9], R T, R vx, R vy, R S0, const DevParams& P) {
+template <class R>
+__device__ __forceinline__ void collide_heat(R g[9], R T, R vx, R vy, R S0, const DevParams& P, R tau_inv = R(0)) {
   const Coefs<R>& C = coefs<R>(P);
   R ns[9];
-  if (P.heat_unit_rates) {
+  if (P.model == 2) {
+    // Gong-Cheng (Eqs. 12-14): BGK with the local 1/tau_g, source G_a = w_a phi, whose moments are
+    // phi (1, -2, 1, 0, ..., 0)
+    R n[9], neq[9];
+    to_moments(g, n);
+    heat_meq(T, vx, vy, 2, neq);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) ns[k] = n[k] - tau_inv * (n[k] - neq[k]);
+    ns[0] += S0;
+    ns[1] += R(-2) * S0;
+    ns[2] += S0;
+  } else if (P.heat_unit_rates) {
     // s_k = 1 for k >= 1: every non-conserved moment relaxes to its equilibrium, so only the zeroth
     // moment (T) and, for Eqs. 54-55, m4 and m6 of g are needed.
     heat_meq(T, vx, vy, P.model, ns);

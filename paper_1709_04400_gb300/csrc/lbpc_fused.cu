@@ -317,15 +317,23 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
     div_lam_gradT = rcv * C.chi * lapT + C.cV_chi * (grx * gTx + gry * gTy);
   }
   const long long i = (long long)gy * P.nx + gx;
-  const R phi = div_lam_gradT * inv_rcv - C.kdiff * lapT + T * (R(1) - dpdT * inv_rcv) * divv;
-  R S0 = phi;
-  if (P.model == 0) {
-    const R pp = first ? phi : phi_prev[i];
-    S0 = phi + R(0.5) * (phi - pp);
+  const R compress = T * (R(1) - dpdT * inv_rcv) * divv;
+  R phi, S0, tau_inv = R(0);
+  if (P.model == 2) {  // Gong-Cheng: Eq. 13 source, local tau_g (Sec. IV A)
+    phi = compress;
+    S0 = phi;
+    tau_inv = R(1) / ((P.lambda_mode == 0 ? R(3) * C.lambda * inv_rcv : R(3) * C.chi) + R(0.5));
+  } else {
+    phi = div_lam_gradT * inv_rcv - C.kdiff * lapT + compress;
+    S0 = phi;
+    if (P.model == 0) {
+      const R pp = first ? phi : phi_prev[i];
+      S0 = phi + R(0.5) * (phi - pp);
+    }
   }
   phi_prev[i] = phi;
   collide_flow(f, rho, vx, vy, Fx, Fy, Q, P);
-  collide_heat(g, T, vx, vy, S0, P);
+  collide_heat(g, T, vx, vy, S0, P, tau_inv);
   pop_store<S, R>(fdst, P.N, i, f, rho, C.wf);
   pop_store<S, R>(gdst, P.N, i, g, T + S0, C.wg);
 }

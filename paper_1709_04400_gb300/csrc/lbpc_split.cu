@@ -180,15 +180,24 @@ __global__ void __launch_bounds__(2 * BLOCK) k_collide(PopBuf<S> fsrc, PopBuf<S>
     gather9(pl.p[P_RHO], P, x, y, c);
     div_lam_gradT = rcv * C.chi * lapT + C.cV_chi * (d_x(c) * gTx + d_y(c) * gTy);
   }
-  // phi: the underlined terms of Eq. 28 with k = (1/s_3 - 1/2) c_s^2
-  const R phi = div_lam_gradT * inv_rcv - C.kdiff * lapT + T * (R(1) - pl.p[P_DPDT][i] * inv_rcv) * divv;
-  R S0 = phi;
-  if (P.model == 0) {  // S0 = phi + 0.5 dt d_t phi, d_t phi ~ [phi(t) - phi(t - dt)]/dt (Eq. 46)
-    const R pp = first ? phi : phi_prev[i];
-    S0 = phi + R(0.5) * (phi - pp);
+  const R compress = T * (R(1) - pl.p[P_DPDT][i] * inv_rcv) * divv;
+  R phi, S0, tau_inv = R(0);
+  if (P.model == 2) {
+    // Gong-Cheng: the source is Eq. 13 alone; tau_g = lambda/(rho c_s^2 c_V) + 1/2 (Sec. IV A)
+    phi = compress;
+    S0 = phi;
+    tau_inv = R(1) / ((P.lambda_mode == 0 ? R(3) * C.lambda * inv_rcv : R(3) * C.chi) + R(0.5));
+  } else {
+    // phi: the underlined terms of Eq. 28 with k = (1/s_3 - 1/2) c_s^2
+    phi = div_lam_gradT * inv_rcv - C.kdiff * lapT + compress;
+    S0 = phi;
+    if (P.model == 0) {  // S0 = phi + 0.5 dt d_t phi, d_t phi ~ [phi(t) - phi(t - dt)]/dt (Eq. 46)
+      const R pp = first ? phi : phi_prev[i];
+      S0 = phi + R(0.5) * (phi - pp);
+    }
   }
   phi_prev[i] = phi;
-  collide_heat(g, T, vx, vy, S0, P);
+  collide_heat(g, T, vx, vy, S0, P, tau_inv);
   pop_store<S, R>(gdst, P.N, i, g, T + S0, C.wg);
 }
 

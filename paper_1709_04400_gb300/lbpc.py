@@ -23,7 +23,7 @@ FP64, FP32, FP16DEV = 0, 1, 2
 PERIODIC, WALL, PRESSURE = 0, 1, 2
 T_NONE, T_DIRICHLET = 0, 1
 LAMBDA_CONST, LAMBDA_RHO_CV_CHI = 0, 1
-IMPROVED, COMPROMISED = 0, 1
+IMPROVED, COMPROMISED, GONG_CHENG = 0, 1, 2
 PATH_AUTO, PATH_SPLIT, PATH_FUSED = 0, 1, 2
 
 EXPORTED = ["lbpc_version", "lbpc_check_params", "lbpc_workspace_bytes", "lbpc_eos_critical", "lbpc_coexistence",
@@ -330,7 +330,7 @@ class Simulation:
 _FLOW = {"periodic": PERIODIC, "wall": WALL, "pressure": PRESSURE}
 _TBC = {"none": T_NONE, "dirichlet": T_DIRICHLET}
 _LAM = {"const": LAMBDA_CONST, "rho_cv_chi": LAMBDA_RHO_CV_CHI}
-_MODEL = {"improved": IMPROVED, "compromised": COMPROMISED}
+_MODEL = {"improved": IMPROVED, "compromised": COMPROMISED, "gong_cheng": GONG_CHENG}
 
 
 def params_from_case(case: dict, prec: int = FP64) -> Params:

@@ -65,9 +65,11 @@ def test_mixed_boundaries_fp64(path):
 
 
 @pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
-def test_compromised_model_fp64(path):
+@pytest.mark.parametrize("mdl", ["compromised", "gong_cheng"])
+def test_comparison_models_fp64(path, mdl):
+    """The comparison models of Sec. IV: compromised (Eq. 44, no corrections) and Gong-Cheng (Eqs. 12-14)."""
     case, rho, T = workloads.mixed_small(TC, RV, RL, nx=33, ny=17)
-    case = dict(case, model="compromised")
+    case = dict(case, model=mdl)
     gpu, *_ = _gpu(case, rho, T, 100, path=path)
     p, s = run_oracle(case, rho, T, 100)
     _assert_within(_errors(gpu, p, s), 1e-10)

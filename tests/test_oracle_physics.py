@@ -128,3 +128,29 @@ def test_d2_law():
     r2 = 1 - ((d2[m] - np.polyval(c, ts[m])) ** 2).sum() / ((d2[m] - d2[m].mean()) ** 2).sum()
     assert c[0] < 0 and r2 > 0.99
     assert d2[-1] < 0.95
+
+
+@pytest.mark.slow
+def test_gong_cheng_decay_and_advection():
+    """Gong-Cheng model (Eqs. 12-14). At rest with uniform rho the source of Eq. 13 vanishes and the BGK
+    diffusivity (tau_g - 1/2) c_s^2 with tau_g = lambda/(rho c_s^2 c_V) + 1/2 is chi = lambda/(rho c_V):
+    a Fourier mode decays at chi q^2 to second order. In a uniform flow the error terms of Eq. 25,
+    d_t0(T v) + div(T v v) = -v (v.grad T) + v (v.grad T), cancel, so an advected Gaussian spreads at chi
+    exactly (unlike the compromised model, whose equilibrium lacks the vv terms)."""
+    rates = []
+    for N in (32, 64):
+        q, rho0 = 2 * np.pi / N, 2.0
+        chi = (2.0 / 3.0) / (rho0 * 5.0)
+        p = model.OracleParams(nx=N, ny=4, frozen_flow=(0.0, 0.0), model="gong_cheng")
+        x = np.arange(N)[None, :] * np.ones((4, 1))
+        s = model.init_state(p, np.full((4, N), rho0), TS + 1e-3 * np.sin(q * x))
+        ts, amp = [], []
+        for _ in range(int(3 / (chi * q * q))):
+            s = model.step(p, s)
+            if s.step >= 10 and s.step % 5 == 0:
+                ts.append(s.step)
+                amp.append(2.0 / N * ((s.g.sum(0)[0] - TS) * np.sin(q * x[0])).sum())
+        rates.append(abs(-np.polyfit(ts, np.log(amp), 1)[0] / (chi * q * q) - 1))
+    assert rates[1] < 0.006 and 3.5 < rates[0] / rates[1] < 4.5
+    _, ratio_gc, _ = _advect("gong_cheng")
+    assert abs(ratio_gc - 1) < 0.005
