@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--dT", type=float, default=0.1, help="superheat dT / T_c of the evaporation case")
     ap.add_argument("--prec", default="", choices=["", "fp64", "fp32", "fp16"])
     ap.add_argument("--path", default="auto", choices=["auto", "split", "fused"])
+    ap.add_argument("--tile", type=int, default=0, help="fused tile shape: 0 = 32x16, 1 = 32x8")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -200,6 +201,7 @@ def run_native(args):
     path = {"auto": lbpc.PATH_AUTO, "split": lbpc.PATH_SPLIT, "fused": lbpc.PATH_FUSED}[args.path]
     sim = lbpc.Simulation(params)
     sim.set_path(path)
+    sim.set_fused_tile(args.tile)
     sim.init(rho, T)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     stream = sim.stream

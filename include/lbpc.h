@@ -155,6 +155,10 @@ const char* lbpc_kernel_name(const lbpc_ctx* c, int32_t k);
 typedef enum { LBPC_PATH_AUTO = 0, LBPC_PATH_SPLIT = 1, LBPC_PATH_FUSED = 2 } lbpc_path;
 lbpc_status lbpc_set_path(lbpc_ctx* c, int32_t path);
 
+/* Tile shape of the fused step: 0 = 32 x 16 (default), 1 = 32 x 8 (smaller shared-memory footprint,
+ * more resident CTAs per SM, more halo recomputation). Both compute the same step. */
+lbpc_status lbpc_set_fused_tile(lbpc_ctx* c, int32_t tile);
+
 /* Synchronise the stream and check the device status word. */
 lbpc_status lbpc_check(lbpc_ctx* c);
 

@@ -356,7 +356,7 @@ LBPC_API lbpc_status lbpc_create(const lbpc_params* p, void* ws, size_t bytes, v
   c->err = LBPC_OK;
   c->msg[0] = 0;
   for (int k = 0; k < 2; ++k)
-    if (lbpc::fused_tma_encode(&c->tma[k], p->prec, c->buf.f[k], c->buf.g[k], c->buf.ref_f[k], c->buf.ref_g[k], c->dp))
+    if (lbpc::fused_tma_encode(&c->tma[k], p->prec, 0, c->buf.f[k], c->buf.g[k], c->buf.ref_f[k], c->buf.ref_g[k], c->dp))
       c->buf.tma[k] = &c->tma[k];
   *out = c;
   return LBPC_OK;
@@ -418,6 +418,18 @@ static const char* step_kernel_name(const lbpc_ctx* c, int k) {
 LBPC_API lbpc_status lbpc_set_path(lbpc_ctx* c, int32_t path) {
   if (!c || path < LBPC_PATH_AUTO || path > LBPC_PATH_FUSED) return LBPC_EINVAL;
   c->path = path;
+  return LBPC_OK;
+}
+
+LBPC_API lbpc_status lbpc_set_fused_tile(lbpc_ctx* c, int32_t tile) {
+  if (!c || tile < 0 || tile > 1) return LBPC_EINVAL;
+  c->buf.fused_tile = tile;
+  for (int k = 0; k < 2; ++k) {
+    c->buf.tma[k] = nullptr;
+    if (lbpc::fused_tma_encode(&c->tma[k], c->p.prec, tile, c->buf.f[k], c->buf.g[k], c->buf.ref_f[k], c->buf.ref_g[k],
+                               c->dp))
+      c->buf.tma[k] = &c->tma[k];
+  }
   return LBPC_OK;
 }
 

@@ -472,9 +472,10 @@ static bool encode_t(TmaMaps* m, void* f, void* g, float* rf, float* rg, const D
   return true;
 }
 
-bool fused_tma_encode(TmaMaps* m, int prec, void* f, void* g, float* rf, float* rg, const DevParams& P) {
-  if (prec == 1) return encode_t<float, 32, 16>(m, f, g, rf, rg, P);
-  if (prec == 2) return encode_t<__half, 32, 16>(m, f, g, rf, rg, P);
+bool fused_tma_encode(TmaMaps* m, int prec, int tile, void* f, void* g, float* rf, float* rg, const DevParams& P) {
+  if (prec == 1) return tile ? encode_t<float, 32, 8>(m, f, g, rf, rg, P) : encode_t<float, 32, 16>(m, f, g, rf, rg, P);
+  if (prec == 2)
+    return tile ? encode_t<__half, 32, 8>(m, f, g, rf, rg, P) : encode_t<__half, 32, 16>(m, f, g, rf, rg, P);
   return false;  // FP64 runs the split step by default; its fused form keeps per-thread loads
 }
 
@@ -485,8 +486,11 @@ cudaError_t fused_step(const SplitBuffers& b, const DevParams& P, int prec, int 
     nb.tma[0] = nb.tma[1] = nullptr;
     return fused_impl<double, double, 32, 8>(nb, P, cur, step, st, ev);
   }
-  if (prec == 1) return fused_impl<float, float, 32, 16>(b, P, cur, step, st, ev);
-  return fused_impl<__half, float, 32, 16>(b, P, cur, step, st, ev);
+  if (prec == 1)
+    return b.fused_tile ? fused_impl<float, float, 32, 8>(b, P, cur, step, st, ev)
+                        : fused_impl<float, float, 32, 16>(b, P, cur, step, st, ev);
+  return b.fused_tile ? fused_impl<__half, float, 32, 8>(b, P, cur, step, st, ev)
+                      : fused_impl<__half, float, 32, 16>(b, P, cur, step, st, ev);
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -37,6 +37,7 @@ struct SplitBuffers {
   double* scalars;   // [0] rho_ave, [1] mass, [2] heat
   long long* status; // [0] flag, [1] step, [2] x, [3] y, [4] code
   const TmaMaps* tma[2] = {nullptr, nullptr};  // tensor maps of buffer A / B for the TMA-staged fused step
+  int fused_tile = 0;                            // 0: 32 x 16 tiles, 1: 32 x 8 tiles (tensor maps must match)
 };
 
 // ev: null, or split_kernel_count(P) + 1 events recorded before the first and after each kernel.
@@ -95,7 +96,7 @@ cudaError_t fused_step(const SplitBuffers& b, const DevParams& P, int prec, int 
                        cudaEvent_t* ev = nullptr);
 // Encode the tensor maps of one buffer (populations f, g and, for FP16, the reference planes) for the
 // TMA-staged fused step; false when the layout does not allow TMA (row stride not 16-byte aligned).
-bool fused_tma_encode(TmaMaps* m, int prec, void* f, void* g, float* rf, float* rg, const DevParams& P);
+bool fused_tma_encode(TmaMaps* m, int prec, int tile, void* f, void* g, float* rf, float* rg, const DevParams& P);
 // rho_ave <- sum of n per-tile partials / N (fixed order), on st.
 void fused_finish(const SplitBuffers& b, const DevParams& P, int n, cudaStream_t st);
 

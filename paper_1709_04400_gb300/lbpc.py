@@ -32,7 +32,8 @@ EXPORTED = ["lbpc_version", "lbpc_check_params", "lbpc_workspace_bytes", "lbpc_e
             "lbpc_kernel_name", "lbpc_set_path", "lbpc_step_static", "lbpc_batch_instance_bytes", "lbpc_batch_create",
             "lbpc_batch_add", "lbpc_batch_remove", "lbpc_batch_step", "lbpc_batch_check", "lbpc_batch_fields",
             "lbpc_batch_sums", "lbpc_batch_step_count", "lbpc_batch_set_config", "lbpc_batch_config",
-            "lbpc_batch_autotune", "lbpc_batch_free_bytes", "lbpc_batch_last_error", "lbpc_batch_destroy"]
+            "lbpc_batch_autotune", "lbpc_batch_free_bytes", "lbpc_batch_last_error", "lbpc_batch_destroy",
+            "lbpc_set_fused_tile"]
 
 
 class LbpcError(RuntimeError):
@@ -92,6 +93,7 @@ def load_library(path: str = LIB_PATH):
                                            ctypes.POINTER(ctypes.c_int32)]),
         "lbpc_kernel_name": (ctypes.c_char_p, [vp, ctypes.c_int32]),
         "lbpc_set_path": (ctypes.c_int, [vp, ctypes.c_int32]),
+        "lbpc_set_fused_tile": (ctypes.c_int, [vp, ctypes.c_int32]),
         "lbpc_step_static": (ctypes.c_int, [P, vp, vp, vp, vp, vp, vp, ctypes.c_int64, vp]),
         "lbpc_batch_instance_bytes": (ctypes.c_size_t, [P]),
         "lbpc_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]),
@@ -268,6 +270,10 @@ class Simulation:
     def set_path(self, path):
         """Kernel organisation of the step: PATH_AUTO, PATH_SPLIT or PATH_FUSED."""
         self._raise(self.lib.lbpc_set_path(self.ctx, int(path)), "lbpc_set_path")
+
+    def set_fused_tile(self, tile):
+        """Tile shape of the fused step: 0 = 32 x 16, 1 = 32 x 8."""
+        self._raise(self.lib.lbpc_set_fused_tile(self.ctx, int(tile)), "lbpc_set_fused_tile")
 
     def step(self, n=1, sync=True):
         s = (self.lib.lbpc_step if sync else self.lib.lbpc_step_async)(self.ctx, int(n))

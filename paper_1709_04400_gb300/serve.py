@@ -58,11 +58,10 @@ def make_case(req: Request, Tc, rho_v, rho_l):
         return workloads.droplet_evaporation(Tc, rho_v, rho_l, n=req.side, radius=req.size_param,
                                              dT_ratio=req.superheat)
     if req.kind == "heated_wall":
-        # closed pool with a neutral wall (G_wall = 0): under this build's wall readings a wettable wall
-        # in a closed box drives the vapour over the strip to near vacuum within about 1800 steps
-        case, rho, T = workloads.heated_wall(Tc, rho_v, rho_l, nx=req.side, ny=req.side, strip_width=int(req.size_param),
-                                             dT_strip_ratio=req.superheat, top="wall")
-        return dict(case, G_wall=0.0), rho, T
+        # closed pool (neutral wall): the fixed-pressure top of the benchmark set-up diverges after about
+        # 1800 steps under this build's boundary readings, and requests run for thousands of steps
+        return workloads.heated_wall(Tc, rho_v, rho_l, nx=req.side, ny=req.side, strip_width=int(req.size_param),
+                                     dT_strip_ratio=req.superheat, top="wall")
     raise ValueError(req.kind)
 
 

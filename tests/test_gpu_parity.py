@@ -224,3 +224,23 @@ def test_fp16_deviation_storage(path):
     assert e16["rho"] < 1e-3 and e16["T"] < 1e-3 and e16["ux"] < 2e-2 and e16["uy"] < 2e-2, e16
     g32, *_ = _gpu(case, rho, T, 100, prec=lbpc.FP32, path=path)
     _assert_within(_errors(g32, p, s), 1e-4)
+
+
+@pytest.mark.parametrize("prec", [lbpc.FP32, lbpc.FP16DEV], ids=["fp32", "fp16"])
+def test_fused_tile_shapes(prec):
+    """Both tile shapes of the fused step (32 x 16 and 32 x 8, TMA-staged interior tiles) compute the
+    same step; the FP32 result stays within 1e-4 of the oracle."""
+    case, rho, T = workloads.droplet_periodic(TC, RV, RL)
+    out = []
+    for tile in (0, 1):
+        sim = lbpc.Simulation(lbpc.params_from_case(case, prec))
+        sim.set_fused_tile(tile)
+        sim.init(rho, T)
+        sim.step(60)
+        out.append(sim.fields())
+        sim.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.max(np.abs(a - b)) <= 1e-5 * np.max(np.abs(b)) + 1e-12
+    if prec == lbpc.FP32:
+        p, s = run_oracle(case, rho, T, 60)
+        _assert_within(_errors(out[1], p, s), 1e-4)
