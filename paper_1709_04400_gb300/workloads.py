@@ -14,7 +14,10 @@ decides whose EOS evaluation supplies them. Nothing here evaluates the lattice B
                        no-slip bottom wall at T_s with a heated strip 20 nodes wide at T_s + 0.3 T_c,
                        top held at the vapour density and T_s, g = 3e-5 downward with buoyancy
                        (rho - rho_ave) g, lambda = rho c_V chi with chi = 0.06 (Sec. IV B).
+  paper_d2_law         the paper's own D^2-law set-up (Sec. IV A): 200 x 200, D0 = 60, dT = 0.14 T_c.
 """
+
+import numpy as np
 
 from . import inputs
 
@@ -89,3 +92,22 @@ def batched_evaporation(Tc, rho_v, rho_l, count=256, side_lo=64, side_hi=512, se
         case, rho, T = droplet_evaporation(Tc, rho_v, rho_l, n=n, radius=radius, dT_ratio=dT)
         out.append((case, rho, T))
     return out
+
+
+
+def paper_d2_law(Tc, rho_v, rho_l, model="improved", lam=2.0 / 3.0):
+    """The droplet-evaporation set-up of Sec. IV A: 200 x 200, a droplet of diameter D0 = 60 at the centre,
+    constant lambda (2/3 in the paper), superheat dT = 0.14 T_c in the vapour and on the boundaries,
+    s3 = s5 = 1, c_V = 5, nu = 0.1, no gravity (flow periodic)."""
+    case, rho, T = droplet_evaporation(Tc, rho_v, rho_l, n=200, radius=30.0, dT_ratio=0.14)
+    return dict(case, name=f"paper_d2_law_{model}_lam{lam:.4g}", model=model, lam=lam), rho, T
+
+
+def droplet_area(rho):
+    """Droplet area from a density field: sum of clip((rho - rho_far)/(rho_centre - rho_far), 0, 1), with
+    rho_far the mean of four near-corner nodes and rho_centre the centre node (self-normalising to the
+    current phase densities)."""
+    ny, nx = rho.shape
+    lo = np.mean([rho[2, 2], rho[2, -3], rho[-3, 2], rho[-3, -3]])
+    hi = rho[ny // 2, nx // 2]
+    return float(np.clip((rho - lo) / (hi - lo), 0.0, 1.0).sum())
