@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--instances", type=int, default=256, help="batched workload: number of instances")
     ap.add_argument("--n", type=int, default=0, help="grid side (0 = the workload's own size)")
     ap.add_argument("--dT", type=float, default=0.1, help="superheat dT / T_c of the evaporation case")
-    ap.add_argument("--prec", default="", choices=["", "fp64", "fp32", "fp16"])
+    ap.add_argument("--prec", default="", choices=["", "fp64", "df64", "fp32", "fp16"])
     ap.add_argument("--path", default="auto", choices=["auto", "split", "fused"])
     ap.add_argument("--tile", type=int, default=0, help="fused tile shape: 0 = 32x16, 1 = 32x8")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -174,6 +174,14 @@ def collide_flops(lambda_mode, unit_heat_rates):
     return 259 + (20 if lambda_mode == "rho_cv_chi" else 0) + (0 if unit_heat_rates else 52)
 
 
+# arithmetic type of each storage precision ("df64": double-word, pairs of binary32 with a 48-bit
+# significand, on the FP32 pipes)
+def _dtypes():
+    from paper_1709_04400_gb300 import lbpc
+
+    return {lbpc.FP64: "f64", lbpc.DF64: "df64 (f32 pair)", lbpc.FP32: "f32", lbpc.FP16DEV: "f32 (f16 storage)"}
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -186,11 +194,12 @@ def run_native(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     build.build()
+    DTYPE = _dtypes()
     p0 = lbpc.Params(nx=8, ny=8)
     Tc, _ = lbpc.eos_critical(p0)
     rv, rl, _ = lbpc.coexistence(p0, 0.86 * Tc)
     case, rho, T, prec_name = make_case(args, Tc, rv, rl)
-    prec = {"fp64": lbpc.FP64, "fp32": lbpc.FP32, "fp16": lbpc.FP16DEV}[prec_name]
+    prec = {"fp64": lbpc.FP64, "df64": lbpc.DF64, "fp32": lbpc.FP32, "fp16": lbpc.FP16DEV}[prec_name]
     params = lbpc.params_from_case(case, prec)
     N = case["nx"] * case["ny"]
 
@@ -245,7 +254,7 @@ def run_native(args):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    pb = {lbpc.FP64: 8, lbpc.FP32: 4, lbpc.FP16DEV: 2}[prec]
+    pb = {lbpc.FP64: 8, lbpc.DF64: 8, lbpc.FP32: 4, lbpc.FP16DEV: 2}[prec]
     peak_bw = float(peaks.get("hbm_gbs", 6800.0))
     bw_src = "MEASURED_PEAKS.json hbm_gbs (burst copy)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
     if prec == lbpc.FP64 and "k_collide" in avg:
@@ -310,7 +319,7 @@ def run_native(args):
             "metric": "coupled flow+thermal MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_s * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if prec == lbpc.FP64 else "f32", "data": "synthetic",
+            "dtype": DTYPE[prec], "data": "synthetic",
             "config": {"workload": case["name"], "nx": case["nx"], "ny": case["ny"], "nodes": N,
                        "storage": prec_name, "parallelism": f"replicas{ws}", "path": args.path,
                        "l2": "flushed before every timed step (512 MiB write); each step timed with CUDA events",

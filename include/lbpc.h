@@ -45,12 +45,20 @@ typedef enum {
   LBPC_ESTATE = 6     /* the context holds an earlier error */
 } lbpc_status;
 
-/* Storage precision of the populations f, g (arithmetic: FP64 for LBPC_FP64, FP32 otherwise).
+/* Storage precision of the populations f, g and the arithmetic of the step.
+ * LBPC_FP64: binary64 storage and arithmetic.
+ * LBPC_FP32: binary32 storage and arithmetic.
  * LBPC_FP16DEV stores each post-collision population as binary16 of its deviation from the rest-state
  * equilibrium w_a * ref of the node that stored it, ref being that node's density (f) or
  * post-collision temperature (g), kept in FP32 planes beside the populations: 2 bytes per population
- * plus 4 per node and set, 96 B per node and step against 152 B for LBPC_FP32. */
-typedef enum { LBPC_FP64 = 0, LBPC_FP32 = 1, LBPC_FP16DEV = 2 } lbpc_prec;
+ * plus 4 per node and set, 96 B per node and step against 152 B for LBPC_FP32. Arithmetic is FP32.
+ * LBPC_DF64: storage and arithmetic in double-word numbers, the unevaluated sum of two binary32
+ * values (48-bit significand, relative precision about 3.6e-15, binary32 exponent range), 8 bytes per
+ * value like LBPC_FP64. Every operation runs on the FP32 pipes; on GPUs whose binary64 rate is a
+ * small fraction of the binary32 rate (GB300: 1/64) the step is several times faster than LBPC_FP64
+ * and follows a binary64 evaluation of the same step to about 1e-12 over thousands of steps.
+ * Inputs and outputs of the API are binary64 for every precision. */
+typedef enum { LBPC_FP64 = 0, LBPC_FP32 = 1, LBPC_FP16DEV = 2, LBPC_DF64 = 3 } lbpc_prec;
 
 /* Flow boundary of an edge. x edges must be periodic; y edges are both periodic or both not.
  * A non-periodic y edge is an on-node row closed by the Zou-He scheme (the paper applies Zou-He at
@@ -151,7 +159,7 @@ const char* lbpc_kernel_name(const lbpc_ctx* c, int32_t k);
  * scratch planes (each EOS evaluated once per node; the faster choice when FP64 arithmetic bounds
  * the step). LBPC_PATH_FUSED: one kernel per step over shared-memory tiles (populations read once
  * and written once; the faster choice when HBM bounds the step). LBPC_PATH_AUTO (default): split
- * for LBPC_FP64, fused for LBPC_FP32 and LBPC_FP16DEV. Both compute the same step. */
+ * for LBPC_FP64 and LBPC_DF64, fused for LBPC_FP32 and LBPC_FP16DEV. Both compute the same step. */
 typedef enum { LBPC_PATH_AUTO = 0, LBPC_PATH_SPLIT = 1, LBPC_PATH_FUSED = 2 } lbpc_path;
 lbpc_status lbpc_set_path(lbpc_ctx* c, int32_t path);
 
@@ -202,8 +210,9 @@ typedef struct lbpc_batch lbpc_batch; /* opaque */
 /* Arena bytes one instance with these parameters takes (0 if the parameters are invalid). */
 size_t lbpc_batch_instance_bytes(const lbpc_params* p);
 
-/* Create an empty batch of at most max_instances instances in storage precision prec over the
- * caller's arena (256-byte aligned, bytes long). Fixed descriptors take a small part of the arena. */
+/* Create an empty batch of at most max_instances instances in storage precision prec (LBPC_FP64,
+ * LBPC_FP32 or LBPC_FP16DEV; LBPC_DF64 returns LBPC_EINVAL) over the caller's arena (256-byte
+ * aligned, bytes long). Fixed descriptors take a small part of the arena. */
 lbpc_status lbpc_batch_create(int32_t prec, int32_t max_instances, void* d_arena, size_t bytes, void* stream,
                               lbpc_batch** out);
 
@@ -258,7 +267,7 @@ void lbpc_batch_destroy(lbpc_batch* b);
  *
  * It runs the same kernels as lbpc_step and lbpc_step_async, with the split organisation.
  *
- *   p         parameters, as for lbpc_create, with prec LBPC_FP64 or LBPC_FP32; nx * ny must not
+ *   p         parameters, as for lbpc_create, with prec LBPC_FP64, LBPC_FP32 or LBPC_DF64; nx * ny must not
  *             exceed LBPC_STATIC_MAX_NODES (LBPC_ENOMEM otherwise, before any device work)
  *   f_in,g_in post-collision populations of the previous step, device, [9][ny][nx] of the storage type
  *             (lbpc_params.prec), D2Q9 order as for lbpc_populations; slot a of node x holds the value

@@ -68,8 +68,8 @@ struct Layout {
 Layout layout_of(const lbpc_params* p) {
   Layout L{};
   L.N = (long long)p->nx * p->ny;
-  L.store = p->prec == LBPC_FP64 ? 8 : (p->prec == LBPC_FP32 ? 4 : 2);
-  L.real = p->prec == LBPC_FP64 ? 8 : 4;
+  L.store = (p->prec == LBPC_FP64 || p->prec == LBPC_DF64) ? 8 : (p->prec == LBPC_FP32 ? 4 : 2);
+  L.real = (p->prec == LBPC_FP64 || p->prec == LBPC_DF64) ? 8 : 4;
   L.nblocks = (int)((L.N + lbpc::split_block() - 1) / lbpc::split_block());
   size_t off = 0;
   const size_t pop = align256(9 * (size_t)L.N * L.store);
@@ -174,6 +174,7 @@ DevParams make_dev_params(const lbpc_params* p) {
   for (int k = 1; k < 9; ++k) d.heat_unit_rates &= p->s_g[k] == 1.0;
   fill_coefs(d.cd, p);
   fill_coefs(d.cf, p);
+  fill_coefs(d.cw, p);
   return d;
 }
 
@@ -231,7 +232,8 @@ LBPC_API lbpc_status lbpc_check_params(const lbpc_params* p, char* msg, size_t n
   if (!p) BAD("params is NULL");
   if (p->nx < 2 || p->ny < 2) BAD("grid %d x %d: nx and ny must be >= 2", p->nx, p->ny);
   if ((long long)p->nx * p->ny > (1ll << 31)) BAD("grid %d x %d exceeds 2^31 nodes", p->nx, p->ny);
-  if (p->prec != LBPC_FP64 && p->prec != LBPC_FP32 && p->prec != LBPC_FP16DEV) BAD("prec %d unknown", p->prec);
+  if (p->prec != LBPC_FP64 && p->prec != LBPC_FP32 && p->prec != LBPC_FP16DEV && p->prec != LBPC_DF64)
+    BAD("prec %d unknown", p->prec);
   if (p->model != LBPC_IMPROVED && p->model != LBPC_COMPROMISED && p->model != LBPC_GONG_CHENG)
     BAD("model %d unknown", p->model);
   if (p->lambda_mode != LBPC_LAMBDA_CONST && p->lambda_mode != LBPC_LAMBDA_RHO_CV_CHI) BAD("lambda_mode %d unknown", p->lambda_mode);
@@ -398,7 +400,8 @@ LBPC_API lbpc_status lbpc_init(lbpc_ctx* c, const double* rho, const double* T, 
 }
 
 static bool use_fused(const lbpc_ctx* c) {
-  return c->path == LBPC_PATH_FUSED || (c->path == LBPC_PATH_AUTO && c->p.prec != LBPC_FP64);
+  return c->path == LBPC_PATH_FUSED ||
+         (c->path == LBPC_PATH_AUTO && c->p.prec != LBPC_FP64 && c->p.prec != LBPC_DF64);
 }
 
 static cudaError_t launch_step(lbpc_ctx* c, cudaEvent_t* ev) {

@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "lbpc_dw.cuh"
+
 namespace lbpc {
 
 enum { BC_PERIODIC = 0, BC_WALL = 1, BC_PRESSURE = 2 };
@@ -53,11 +55,13 @@ struct DevParams {
   int heat_unit_rates;  // s_g[1..8] all 1: the thermal relaxation sets every non-conserved moment to m_eq
   Coefs<double> cd;
   Coefs<float> cf;
+  Coefs<dw> cw;  // double-word arithmetic (LBPC_DF64)
 };
 
 template <class R> __host__ __device__ __forceinline__ const Coefs<R>& coefs(const DevParams& P);
 template <> __host__ __device__ __forceinline__ const Coefs<double>& coefs<double>(const DevParams& P) { return P.cd; }
 template <> __host__ __device__ __forceinline__ const Coefs<float>& coefs<float>(const DevParams& P) { return P.cf; }
+template <> __host__ __device__ __forceinline__ const Coefs<dw>& coefs<dw>(const DevParams& P) { return P.cw; }
 
 // ------------------------------------------------------------------------------------------------
 // moment transforms: m = M x and x = M^{-1} m with M^{-1} = M^T diag(1/9,1/36,1/36,1/6,1/12,1/6,1/12,1/4,1/4)
@@ -69,12 +73,12 @@ template <class R> __device__ __forceinline__ void to_moments(const R x[9], R m[
   const R px = x[5] - x[6] - x[7] + x[8];
   const R py = x[5] + x[6] - x[7] - x[8];
   m[0] = x[0] + s14 + s58;
-  m[1] = R(-4) * x[0] - s14 + R(2) * s58;
-  m[2] = R(4) * x[0] - R(2) * s14 + s58;
+  m[1] = x[0] * -4 - s14 + s58 * 2;
+  m[2] = x[0] * 4 - s14 * 2 + s58;
   m[3] = d13 + px;
-  m[4] = R(-2) * d13 + px;
+  m[4] = d13 * -2 + px;
   m[5] = d24 + py;
-  m[6] = R(-2) * d24 + py;
+  m[6] = d24 * -2 + py;
   m[7] = x[1] - x[2] + x[3] - x[4];
   m[8] = x[5] - x[6] + x[7] - x[8];
 }
@@ -83,11 +87,11 @@ template <class R> __device__ __forceinline__ void from_moments(const R m[9], R 
   const R u0 = m[0] * R(1.0 / 9.0), u1 = m[1] * R(1.0 / 36.0), u2 = m[2] * R(1.0 / 36.0);
   const R u3 = m[3] * R(1.0 / 6.0), u4 = m[4] * R(1.0 / 12.0), u5 = m[5] * R(1.0 / 6.0);
   const R u6 = m[6] * R(1.0 / 12.0), u7 = m[7] * R(0.25), u8 = m[8] * R(0.25);
-  const R ax = u0 - u1 - R(2) * u2;  // common to e1..e4
-  const R dg = u0 + R(2) * u1 + u2;  // common to e5..e8
-  const R qx = u3 - R(2) * u4, qy = u5 - R(2) * u6;
+  const R ax = u0 - u1 - u2 * 2;  // common to e1..e4
+  const R dg = u0 + u1 * 2 + u2;  // common to e5..e8
+  const R qx = u3 - u4 * 2, qy = u5 - u6 * 2;
   const R sx = u3 + u4, sy = u5 + u6;
-  x[0] = u0 - R(4) * u1 + R(4) * u2;
+  x[0] = u0 - u1 * 4 + u2 * 4;
   x[1] = ax + qx + u7;
   x[2] = ax + qy - u7;
   x[3] = ax - qx + u7;
@@ -114,7 +118,7 @@ template <class R> __device__ __forceinline__ void eos(R rho, R T, const DevPara
   // 1/(1 - b rho) and 1/(1 + 2 b rho - b^2 rho^2) (and 1/rho if asked) from one reciprocal
   const R br = C.b * rho;
   const R d1 = R(1) - br;
-  const R d2 = R(1) + R(2) * br - br * br;
+  const R d2 = R(1) + br * 2 - br * br;
   const R d12 = d1 * d2;
   R r12;
   if (inv_rho) {
@@ -150,6 +154,8 @@ template <class S, class R>
 __device__ __forceinline__ R pop_load(const PopBuf<S>& b, long long N, int a, long long idx, const R* w) {
   if constexpr (is_half_t<S>::value) {
     return R(__half2float(__ldg(b.p + (long long)a * N + idx))) + w[a] * R(__ldg(b.ref + idx));
+  } else if constexpr (is_dw_t<S>::value) {
+    return R(ldgv(b.p + (long long)a * N + idx));
   } else {
     return R(__ldg(b.p + (long long)a * N + idx));
   }
@@ -201,24 +207,24 @@ template <class R> __device__ __forceinline__ void flow_closure(R f[9], const De
   if (y == 0) {
     if (P.ybc_lo == BC_WALL) {
       f[2] = f[4];
-      f[5] = f[7] - R(0.5) * d13;
-      f[6] = f[8] + R(0.5) * d13;
+      f[5] = f[7] - d13 * 0.5f;
+      f[6] = f[8] + d13 * 0.5f;
     } else {
-      const R ru = C.rho_bc_lo - (f[0] + f[1] + f[3] + R(2) * (f[4] + f[7] + f[8]));  // rho_bc u_y
+      const R ru = C.rho_bc_lo - (f[0] + f[1] + f[3] + (f[4] + f[7] + f[8]) * 2);  // rho_bc u_y
       f[2] = f[4] + R(2.0 / 3.0) * ru;
-      f[5] = f[7] - R(0.5) * d13 + ru * R(1.0 / 6.0);
-      f[6] = f[8] + R(0.5) * d13 + ru * R(1.0 / 6.0);
+      f[5] = f[7] - d13 * 0.5f + ru * R(1.0 / 6.0);
+      f[6] = f[8] + d13 * 0.5f + ru * R(1.0 / 6.0);
     }
   } else if (y == P.ny - 1) {
     if (P.ybc_hi == BC_WALL) {
       f[4] = f[2];
-      f[7] = f[5] + R(0.5) * d13;
-      f[8] = f[6] - R(0.5) * d13;
+      f[7] = f[5] + d13 * 0.5f;
+      f[8] = f[6] - d13 * 0.5f;
     } else {
-      const R ru = (f[0] + f[1] + f[3] + R(2) * (f[2] + f[5] + f[6])) - C.rho_bc_hi;  // rho_bc u_y
+      const R ru = (f[0] + f[1] + f[3] + (f[2] + f[5] + f[6]) * 2) - C.rho_bc_hi;  // rho_bc u_y
       f[4] = f[2] - R(2.0 / 3.0) * ru;
-      f[7] = f[5] + R(0.5) * d13 - ru * R(1.0 / 6.0);
-      f[8] = f[6] - R(0.5) * d13 - ru * R(1.0 / 6.0);
+      f[7] = f[5] + d13 * 0.5f - ru * R(1.0 / 6.0);
+      f[8] = f[6] - d13 * 0.5f - ru * R(1.0 / 6.0);
     }
   }
 }
@@ -229,8 +235,8 @@ template <class R> __device__ __forceinline__ void heat_meq(R T, R vx, R vy, int
   if (model == 2) {
     const R v2 = vx * vx + vy * vy;
     n[0] = T;
-    n[1] = T * (R(-2) + R(3) * v2);
-    n[2] = T * (R(1) - R(3) * v2);
+    n[1] = T * (R(-2) + v2 * 3);
+    n[2] = T * (R(1) - v2 * 3);
     n[3] = T * vx;
     n[4] = -T * vx;
     n[5] = T * vy;
@@ -240,8 +246,8 @@ template <class R> __device__ __forceinline__ void heat_meq(R T, R vx, R vy, int
     return;
   }
   n[0] = T;
-  n[1] = R(-2) * T;
-  n[2] = model == 0 ? R(2) * T : T;
+  n[1] = T * -2;
+  n[2] = model == 0 ? T * 2 : T;
   n[3] = T * vx;
   n[4] = -T * vx;
   n[5] = T * vy;
@@ -263,9 +269,9 @@ template <class R> __device__ __forceinline__ void heat_closure(R g[9], const De
         R n[9], e[9];
         heat_meq(Tb, R(0), R(0), P.model, n);
         from_moments(n, e);
-        g[2] = R(2) * e[2] - g[4];
-        g[5] = R(2) * e[5] - g[7];
-        g[6] = R(2) * e[6] - g[8];
+        g[2] = e[2] * 2 - g[4];
+        g[5] = e[5] * 2 - g[7];
+        g[6] = e[6] * 2 - g[8];
       } else {
         g[2] = g[4]; g[5] = g[7]; g[6] = g[8];
       }
@@ -275,9 +281,9 @@ template <class R> __device__ __forceinline__ void heat_closure(R g[9], const De
         R n[9], e[9];
         heat_meq(C.T_bc[3], R(0), R(0), P.model, n);
         from_moments(n, e);
-        g[4] = R(2) * e[4] - g[2];
-        g[7] = R(2) * e[7] - g[5];
-        g[8] = R(2) * e[8] - g[6];
+        g[4] = e[4] * 2 - g[2];
+        g[7] = e[7] * 2 - g[5];
+        g[8] = e[8] * 2 - g[6];
       } else {
         g[4] = g[2]; g[7] = g[5]; g[8] = g[6];
       }
@@ -326,11 +332,11 @@ __device__ __forceinline__ void collide_flow(R f[9], R rho, R vx, R vy, R Fx, R 
   m[3] += Fx;
   m[5] += Fy;
   R meq[9], SF[9];
-  meq[1] = rho * (R(-2) + R(3) * v2); SF[1] = R(6) * vF + Q;
-  meq[2] = rho * (R(1) - R(3) * v2);  SF[2] = R(-6) * vF - Q;
+  meq[1] = rho * (R(-2) + v2 * 3); SF[1] = vF * 6 + Q;
+  meq[2] = rho * (R(1) - v2 * 3);  SF[2] = vF * -6 - Q;
   meq[4] = -rho * vx;                 SF[4] = -Fx;
   meq[6] = -rho * vy;                 SF[6] = -Fy;
-  meq[7] = rho * (vxx - vyy);         SF[7] = R(2) * (vx * Fx - vy * Fy);
+  meq[7] = rho * (vxx - vyy);         SF[7] = (vx * Fx - vy * Fy) * 2;
   meq[8] = rho * vx * vy;             SF[8] = vx * Fy + vy * Fx;
 #pragma unroll
   for (int k = 1; k < 9; ++k) {
@@ -355,7 +361,7 @@ __device__ __forceinline__ void collide_heat(R g[9], R T, R vx, R vy, R S0, cons
 #pragma unroll
     for (int k = 0; k < 9; ++k) ns[k] = n[k] - tau_inv * (n[k] - neq[k]);
     ns[0] += S0;
-    ns[1] += R(-2) * S0;
+    ns[1] += S0 * -2;
     ns[2] += S0;
   } else if (P.heat_unit_rates) {
     // s_k = 1 for k >= 1: every non-conserved moment relaxes to its equilibrium, so only the zeroth
@@ -363,8 +369,8 @@ __device__ __forceinline__ void collide_heat(R g[9], R T, R vx, R vy, R S0, cons
     heat_meq(T, vx, vy, P.model, ns);
     ns[0] = T + S0;
     if (P.model == 0) {
-      const R n4 = R(-2) * (g[1] - g[3]) + (g[5] - g[6] - g[7] + g[8]);
-      const R n6 = R(-2) * (g[2] - g[4]) + (g[5] + g[6] - g[7] - g[8]);
+      const R n4 = (g[1] - g[3]) * -2 + (g[5] - g[6] - g[7] + g[8]);
+      const R n6 = (g[2] - g[4]) * -2 + (g[5] + g[6] - g[7] - g[8]);
       ns[3] += C.c3 * (n4 - ns[4]);
       ns[5] += C.c5 * (n6 - ns[6]);
     }

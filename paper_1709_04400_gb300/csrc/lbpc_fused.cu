@@ -239,8 +239,8 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
     Fx = -C.G * pc * sx;
     Fy = -C.G * pc * sy;
     if (!INTERIOR && !P.yper) {
-      if (y == 0 && P.ybc_lo == BC_WALL) Fy += R(0.5) * C.G_wall * pc;
-      if (y == P.ny - 1 && P.ybc_hi == BC_WALL) Fy -= R(0.5) * C.G_wall * pc;
+      if (y == 0 && P.ybc_lo == BC_WALL) Fy += C.G_wall * 0.5f * pc;
+      if (y == P.ny - 1 && P.ybc_hi == BC_WALL) Fy -= C.G_wall * 0.5f * pc;
     }
     const R rr = s_rho[hy][hx];
     if (P.buoyancy) {
@@ -250,8 +250,8 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
     }
     Q = C.qG2 * (sx * sx + sy * sy);
     const R ir = R(1) / rr;
-    vx = (s_jx[hy][hx] + R(0.5) * Fx) * ir;
-    vy = (s_jy[hy][hx] + R(0.5) * Fy) * ir;
+    vx = (s_jx[hy][hx] + Fx * 0.5f) * ir;
+    vy = (s_jy[hy][hx] + Fy * 0.5f) * ir;
   };
   // region row (stage-1 coordinates) holding the clamped domain row of stage-1 row hy
   auto clamp_hy = [&](int hy) {
@@ -296,8 +296,8 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
                 (s_T[hy + 1][hx + 1] - s_T[hy + 1][hx - 1] - s_T[hy - 1][hx - 1] + s_T[hy - 1][hx + 1]) * R(1.0 / 12.0);
   const R gTy = (s_T[hy + 1][hx] - s_T[hy - 1][hx]) * R(1.0 / 3.0) +
                 (s_T[hy + 1][hx + 1] + s_T[hy + 1][hx - 1] - s_T[hy - 1][hx - 1] - s_T[hy - 1][hx + 1]) * R(1.0 / 12.0);
-  const R lapT = (s_T[hy][hx + 1] + s_T[hy][hx - 1] + s_T[hy + 1][hx] + s_T[hy - 1][hx] - R(4) * T) * R(2.0 / 3.0) +
-                 (s_T[hy + 1][hx + 1] + s_T[hy + 1][hx - 1] + s_T[hy - 1][hx - 1] + s_T[hy - 1][hx + 1] - R(4) * T) *
+  const R lapT = (s_T[hy][hx + 1] + s_T[hy][hx - 1] + s_T[hy + 1][hx] + s_T[hy - 1][hx] - T * 4) * R(2.0 / 3.0) +
+                 (s_T[hy + 1][hx + 1] + s_T[hy + 1][hx - 1] + s_T[hy - 1][hx - 1] + s_T[hy - 1][hx + 1] - T * 4) *
                      R(1.0 / 6.0);
   const int ux = tx + 1, uy = ty + 1;  // stage-2 coordinates
   const R divv = (s_vx[uy][ux + 1] - s_vx[uy][ux - 1]) * R(1.0 / 3.0) +
@@ -322,13 +322,13 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
   if (P.model == 2) {  // Gong-Cheng: Eq. 13 source, local tau_g (Sec. IV A)
     phi = compress;
     S0 = phi;
-    tau_inv = R(1) / ((P.lambda_mode == 0 ? R(3) * C.lambda * inv_rcv : R(3) * C.chi) + R(0.5));
+    tau_inv = R(1) / ((P.lambda_mode == 0 ? C.lambda * 3 * inv_rcv : C.chi * 3) + R(0.5));
   } else {
     phi = div_lam_gradT * inv_rcv - C.kdiff * lapT + compress;
     S0 = phi;
     if (P.model == 0) {
       const R pp = first ? phi : phi_prev[i];
-      S0 = phi + R(0.5) * (phi - pp);
+      S0 = phi + (phi - pp) * 0.5f;
     }
   }
   phi_prev[i] = phi;
@@ -405,19 +405,23 @@ static cudaError_t fused_impl(const SplitBuffers& b, const DevParams& P, int cur
   const PopBuf<S> fs{(S*)b.f[cur], b.ref_f[cur]}, gs{(S*)b.g[cur], b.ref_g[cur]};
   const PopBuf<S> fd{(S*)b.f[cur ^ 1], b.ref_f[cur ^ 1]}, gd{(S*)b.g[cur ^ 1], b.ref_g[cur ^ 1]};
   if (ev) cudaEventRecord(ev[0], st);
-  if (b.tma[cur]) {
-    using B = TmaBox<S, TX, TY>;
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_fused_tma<S, R, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, B::BYTES);
-      attr = true;
+  bool staged = false;
+  if constexpr (sizeof(S) <= 4) {  // the TMA-staged kernel exists for FP32 and FP16 storage
+    if (b.tma[cur]) {
+      using B = TmaBox<S, TX, TY>;
+      static bool attr = false;
+      if (!attr) {
+        cudaFuncSetAttribute(k_fused_tma<S, R, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, B::BYTES);
+        attr = true;
+      }
+      k_fused_tma<S, R, TX, TY><<<grid, TX * TY, B::BYTES, st>>>(fs, gs, fd, gd, (R*)b.phi_prev, P, step, step == 0,
+                                                                 b.scalars, b.partials, b.status, *b.tma[cur]);
+      staged = true;
     }
-    k_fused_tma<S, R, TX, TY><<<grid, TX * TY, B::BYTES, st>>>(fs, gs, fd, gd, (R*)b.phi_prev, P, step, step == 0,
-                                                               b.scalars, b.partials, b.status, *b.tma[cur]);
-  } else {
+  }
+  if (!staged)
     k_fused<S, R, TX, TY><<<grid, TX * TY, 0, st>>>(fs, gs, fd, gd, (R*)b.phi_prev, P, step, step == 0, b.scalars,
                                                     b.partials, b.status);
-  }
   if (ev) cudaEventRecord(ev[1], st);
   if (P.buoyancy) {
     fused_finish(b, P, (int)(grid.x * grid.y), st);
@@ -485,6 +489,11 @@ cudaError_t fused_step(const SplitBuffers& b, const DevParams& P, int prec, int 
     SplitBuffers nb = b;
     nb.tma[0] = nb.tma[1] = nullptr;
     return fused_impl<double, double, 32, 8>(nb, P, cur, step, st, ev);
+  }
+  if (prec == 3) {
+    SplitBuffers nb = b;
+    nb.tma[0] = nb.tma[1] = nullptr;
+    return fused_impl<dw, dw, 32, 8>(nb, P, cur, step, st, ev);
   }
   if (prec == 1)
     return b.fused_tile ? fused_impl<float, float, 32, 8>(b, P, cur, step, st, ev)

@@ -44,9 +44,9 @@ template <class R> __device__ __forceinline__ void gather9(const R* __restrict__
   for (int dy = -1; dy <= 1; ++dy) {
     bool lo, hi;
     const long long row = (long long)nb_row(P, y, dy, lo, hi) * P.nx;
-    c[dy + 1][0] = __ldg(X + row + xm);
-    c[dy + 1][1] = __ldg(X + row + x);
-    c[dy + 1][2] = __ldg(X + row + xp);
+    c[dy + 1][0] = ldgv(X + row + xm);
+    c[dy + 1][1] = ldgv(X + row + x);
+    c[dy + 1][2] = ldgv(X + row + xp);
   }
 }
 
@@ -60,8 +60,8 @@ template <class R> __device__ __forceinline__ R d_y(const R c[3][3]) {
 }
 template <class R> __device__ __forceinline__ R lap(const R c[3][3]) {
   const R ctr = c[1][1];
-  return (c[1][2] + c[1][0] + c[2][1] + c[0][1] - R(4) * ctr) * R(2.0 / 3.0) +
-         (c[2][2] + c[2][0] + c[0][0] + c[0][2] - R(4) * ctr) * R(1.0 / 6.0);
+  return (c[1][2] + c[1][0] + c[2][1] + c[0][1] - ctr * 4) * R(2.0 / 3.0) +
+         (c[2][2] + c[2][0] + c[0][0] + c[0][2] - ctr * 4) * R(1.0 / 6.0);
 }
 
 template <class S, class R>
@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(BLOCK) k_force(Planes<R> pl, DevParams P, cons
   R Fx = Fix, Fy = Fiy;
   // F_ads = -G_w psi(x) sum_a w_a s(x+e_a) e_a: the solid ghost row gives sum = (0, -1/2) below, (0, 1/2) above.
   if (!P.yper) {
-    if (y == 0 && P.ybc_lo == BC_WALL) Fy += R(0.5) * C.G_wall * pc;
-    if (y == P.ny - 1 && P.ybc_hi == BC_WALL) Fy -= R(0.5) * C.G_wall * pc;
+    if (y == 0 && P.ybc_lo == BC_WALL) Fy += C.G_wall * 0.5f * pc;
+    if (y == P.ny - 1 && P.ybc_hi == BC_WALL) Fy -= C.G_wall * 0.5f * pc;
   }
   const R rho = pl.p[P_RHO][i];
   if (P.buoyancy) {  // F_b = (rho - rho_ave) g (Sec. IV B)
@@ -128,8 +128,8 @@ __global__ void __launch_bounds__(BLOCK) k_force(Planes<R> pl, DevParams P, cons
     Fy += dr * C.gy;
   }
   const R inv_rho = pl.p[P_IRHO][i];
-  pl.p[P_VX][i] = (pl.p[P_JX][i] + R(0.5) * Fx) * inv_rho;
-  pl.p[P_VY][i] = (pl.p[P_JY][i] + R(0.5) * Fy) * inv_rho;
+  pl.p[P_VX][i] = (pl.p[P_JX][i] + Fx * 0.5f) * inv_rho;
+  pl.p[P_VY][i] = (pl.p[P_JY][i] + Fy * 0.5f) * inv_rho;
   pl.p[P_FX][i] = Fx;
   pl.p[P_FY][i] = Fy;
   // sigma term Q = qcoef |F_int|^2 / psi^2 = qcoef G^2 (sx^2 + sy^2): psi^2 cancels
@@ -186,14 +186,14 @@ __global__ void __launch_bounds__(2 * BLOCK) k_collide(PopBuf<S> fsrc, PopBuf<S>
     // Gong-Cheng: the source is Eq. 13 alone; tau_g = lambda/(rho c_s^2 c_V) + 1/2 (Sec. IV A)
     phi = compress;
     S0 = phi;
-    tau_inv = R(1) / ((P.lambda_mode == 0 ? R(3) * C.lambda * inv_rcv : R(3) * C.chi) + R(0.5));
+    tau_inv = R(1) / ((P.lambda_mode == 0 ? C.lambda * 3 * inv_rcv : C.chi * 3) + R(0.5));
   } else {
     // phi: the underlined terms of Eq. 28 with k = (1/s_3 - 1/2) c_s^2
     phi = div_lam_gradT * inv_rcv - C.kdiff * lapT + compress;
     S0 = phi;
     if (P.model == 0) {  // S0 = phi + 0.5 dt d_t phi, d_t phi ~ [phi(t) - phi(t - dt)]/dt (Eq. 46)
       const R pp = first ? phi : phi_prev[i];
-      S0 = phi + R(0.5) * (phi - pp);
+      S0 = phi + (phi - pp) * 0.5f;
     }
   }
   phi_prev[i] = phi;
@@ -343,6 +343,7 @@ cudaError_t split_step(const SplitBuffers& b, const DevParams& P, int prec, int 
                        cudaEvent_t* ev) {
   if (prec == 0) return step_impl<double, double>(b, P, cur, step, st, ev);
   if (prec == 1) return step_impl<float, float>(b, P, cur, step, st, ev);
+  if (prec == 3) return step_impl<dw, dw>(b, P, cur, step, st, ev);
   return step_impl<__half, float>(b, P, cur, step, st, ev);
 }
 
@@ -368,6 +369,7 @@ cudaError_t split_init(const SplitBuffers& b, const DevParams& P, int prec, cons
                        const double* ux, const double* uy, cudaStream_t st) {
   if (prec == 0) return init_impl<double>(b, P, rho, T, ux, uy, st);
   if (prec == 1) return init_impl<float>(b, P, rho, T, ux, uy, st);
+  if (prec == 3) return init_impl<dw>(b, P, rho, T, ux, uy, st);
   return init_impl<__half>(b, P, rho, T, ux, uy, st);
 }
 
@@ -382,6 +384,7 @@ static cudaError_t sums_impl(const SplitBuffers& b, const DevParams& P, int cur,
 cudaError_t split_sums(const SplitBuffers& b, const DevParams& P, int prec, int cur, cudaStream_t st) {
   if (prec == 0) return sums_impl<double>(b, P, cur, st);
   if (prec == 1) return sums_impl<float>(b, P, cur, st);
+  if (prec == 3) return sums_impl<dw>(b, P, cur, st);
   return sums_impl<__half>(b, P, cur, st);
 }
 
@@ -400,6 +403,7 @@ cudaError_t split_fields(const SplitBuffers& b, const DevParams& P, int prec, in
                          double* ux, double* uy, double* T, cudaStream_t st) {
   if (prec == 0) return fields_impl<double, double>(b, P, cur, step, rho, ux, uy, T, st);
   if (prec == 1) return fields_impl<float, float>(b, P, cur, step, rho, ux, uy, T, st);
+  if (prec == 3) return fields_impl<dw, dw>(b, P, cur, step, rho, ux, uy, T, st);
   return fields_impl<__half, float>(b, P, cur, step, rho, ux, uy, T, st);
 }
 
@@ -410,6 +414,8 @@ cudaError_t split_export_pops(const SplitBuffers& b, const DevParams& P, int pre
     k_export_pops<double><<<nb, BLOCK, 0, st>>>(fbuf<double>(b, cur), gbuf<double>(b, cur), P, which, only, out);
   else if (prec == 1)
     k_export_pops<float><<<nb, BLOCK, 0, st>>>(fbuf<float>(b, cur), gbuf<float>(b, cur), P, which, only, out);
+  else if (prec == 3)
+    k_export_pops<dw><<<nb, BLOCK, 0, st>>>(fbuf<dw>(b, cur), gbuf<dw>(b, cur), P, which, only, out);
   else
     k_export_pops<__half><<<nb, BLOCK, 0, st>>>(fbuf<__half>(b, cur), gbuf<__half>(b, cur), P, which, only, out);
   return cudaGetLastError();

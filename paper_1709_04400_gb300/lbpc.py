@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "liblbpc.so")
 LBPC_OK, LBPC_EINVAL, LBPC_ENOMEM, LBPC_ECUDA, LBPC_ENONPHYS, LBPC_ETIMEOUT, LBPC_ESTATE = range(7)
 STATUS_NAMES = {0: "LBPC_OK", 1: "LBPC_EINVAL", 2: "LBPC_ENOMEM", 3: "LBPC_ECUDA", 4: "LBPC_ENONPHYS",
                 5: "LBPC_ETIMEOUT", 6: "LBPC_ESTATE"}
-FP64, FP32, FP16DEV = 0, 1, 2
+FP64, FP32, FP16DEV, DF64 = 0, 1, 2, 3  # DF64: double-word (pairs of binary32) storage and arithmetic
 PERIODIC, WALL, PRESSURE = 0, 1, 2
 T_NONE, T_DIRICHLET = 0, 1
 LAMBDA_CONST, LAMBDA_RHO_CV_CHI = 0, 1

@@ -71,6 +71,8 @@ def test_workspace_grows_with_grid(lib):
     # FP64: 4 x 9 population planes + phi + 12 scratch planes = 49 planes of 8 bytes per node
     assert 49 * 8 * 128 * 128 <= w2 < 49 * 8 * 128 * 128 + 64 * 1024
     assert w2 > 3.9 * w1 and w3 < 0.55 * w2
+    # double-word storage and arithmetic: 8 bytes per value like FP64
+    assert lbpc.workspace_bytes(lbpc.Params(nx=128, ny=128, prec=lbpc.DF64)) == w2
 
 
 def test_eos_helpers_match_oracle(lib):
