@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--tile", type=int, default=0, help="fused tile shape: 0 = 32x16, 1 = 32x8")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the double-word (DF64) variant of an FP64 run")
     return ap.parse_args()
 
 
@@ -278,6 +279,35 @@ def run_native(args):
                 "frac": achieved / peak_bw, "traffic": None, "peak_source": bw_src,
                 "bytes_per_node": collide_bytes_per_node(pb), "top_kernel": top}
 
+    # the same workload in double-word arithmetic (LBPC_DF64: pairs of binary32 on the FP32 pipes, held
+    # to the FP64 parity bar by the tests), timed the same way, beside the binary64 headline
+    variants = None
+    if prec == lbpc.FP64 and not args.no_variants:
+        vsim = lbpc.Simulation(lbpc.params_from_case(case, lbpc.DF64))
+        vsim.set_path(path)
+        vsim.init(rho, T)
+        vk = {}
+
+        def vstep():
+            with torch.cuda.stream(vsim.stream):
+                flush.zero_()
+            return vsim.step_timed()
+
+        for _ in range(args.warmup):
+            vstep()
+        for _ in range(args.steps):
+            for k, v in vstep().items():
+                vk.setdefault(k, []).append(v)
+        vsim.close()
+        vms = {k: sum(v) / len(v) for k, v in vk.items()}
+        vstep_ms = sum(vms.values())
+        vtop = max(vms, key=vms.get)
+        variants = {"df64": {"value": N / (vstep_ms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": vstep_ms,
+                             "dtype": "df64 (f32 pair, 48-bit significand)", "kernel_ms": vms,
+                             "top_kernel": vtop,
+                             "top_kernel_hbm_frac": collide_bytes_per_node(8) * N / (vms[vtop] / 1e3) / 1e9 / peak_bw
+                             if vtop == "k_collide" else None}}
+
     e2e = None
     if not args.no_e2e:
         # end to end through the public API with pinned host buffers: H2D of the initial fields,
@@ -324,7 +354,7 @@ def run_native(args):
                        "storage": prec_name, "parallelism": f"replicas{ws}", "path": args.path,
                        "l2": "flushed before every timed step (512 MiB write); each step timed with CUDA events",
                        "wall_ms_per_step": wall * 1e3 / args.steps},
-            "roofline": roof, "cpu_baseline": base, "e2e": e2e,
+            "roofline": roof, "cpu_baseline": base, "e2e": e2e, "variants": variants,
             "gpu_launches": nk * args.steps,
             "kernel_ms": {k: sum(v) / len(v) for k, v in per_kernel.items()},
             "clocks": clocks,

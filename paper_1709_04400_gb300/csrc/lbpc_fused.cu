@@ -511,7 +511,7 @@ cudaError_t fused_step(const SplitBuffers& b, const DevParams& P, int prec, int 
 // valid when instances join or leave.
 // ------------------------------------------------------------------------------------------------
 template <class S, class R, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY) k_batch_step(const BatchMeta* __restrict__ meta,
+__global__ void __launch_bounds__(TX* TY, sizeof(S) <= 4 ? 1024 / (TX * TY) : 1) k_batch_step(const BatchMeta* __restrict__ meta,
                                                        const BatchInst<S>* __restrict__ insts) {
   __shared__ FusedSmem<R, TX, TY> sm;
   __shared__ DevParams sP;
