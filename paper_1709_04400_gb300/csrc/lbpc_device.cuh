@@ -41,8 +41,10 @@ template <class R> struct Coefs {
   R wg[9];      // rest-state equilibrium weights of g: M^{-1} m_eq(T = 1, v = 0) of the thermal model
 };
 
-// Everything a kernel needs, derived once on the host from lbpc_params and passed by value.
-struct DevParams {
+// Everything a kernel needs, derived once on the host from lbpc_params and passed by value. The
+// coefficient sets start on 16-byte boundaries so that a kernel can copy the header and the one set
+// it uses with 16-byte asynchronous copies.
+struct alignas(16) DevParams {
   int nx, ny;
   long long N;       // nx * ny
   int yper;          // y periodic
@@ -53,9 +55,9 @@ struct DevParams {
   int lambda_mode;   // 0 const, 1 rho cV chi
   int buoyancy;
   int heat_unit_rates;  // s_g[1..8] all 1: the thermal relaxation sets every non-conserved moment to m_eq
-  Coefs<double> cd;
-  Coefs<float> cf;
-  Coefs<dw> cw;  // double-word arithmetic (LBPC_DF64)
+  alignas(16) Coefs<double> cd;
+  alignas(16) Coefs<float> cf;
+  alignas(16) Coefs<dw> cw;  // double-word arithmetic (LBPC_DF64)
 };
 
 template <class R> __host__ __device__ __forceinline__ const Coefs<R>& coefs(const DevParams& P);

@@ -504,40 +504,99 @@ cudaError_t fused_step(const SplitBuffers& b, const DevParams& P, int prec, int 
 
 // ------------------------------------------------------------------------------------------------
 // Batched step: many independent instances of uneven size in one persistent launch. CTAs walk a work
-// list of (instance, tile) entries round-robin; each tile runs the same body as the single-instance
-// kernel with that instance's parameters (copied to shared memory when the instance changes) and
-// buffers, so an instance's result does not depend on what else is in the batch. The tile count and
-// every per-instance value live in device memory, so a captured CUDA graph of these launches stays
-// valid when instances join or leave.
+// list of (instance, tile) entries round-robin (the tiles in flight at any moment form one compact
+// band of the list, so neighbouring tiles' halos meet in L2); each tile runs the same body as the
+// single-instance kernel with that instance's parameters and buffers, so an instance's result does
+// not depend on what else is in the batch. The tile count and every per-instance value live in
+// device memory, so a captured CUDA graph of these launches stays valid when instances join or leave.
+//
+// The walk is software-pipelined: while a tile computes, the CTA already holds the next tile's list
+// entry and copies the next instance's descriptor (integer header, the coefficient set of the
+// arithmetic type, buffer pointers and step state) into the second of two shared-memory slots with
+// 16-byte asynchronous copies, so a change of instance costs no exposed global-memory latency.
 // ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <class R> struct CoefSpan;  // byte range of the coefficient set a kernel of arithmetic R reads
+template <> struct CoefSpan<double> { static constexpr size_t off = offsetof(DevParams, cd), len = sizeof(Coefs<double>); };
+template <> struct CoefSpan<float> { static constexpr size_t off = offsetof(DevParams, cf), len = sizeof(Coefs<float>); };
+template <> struct CoefSpan<dw> { static constexpr size_t off = offsetof(DevParams, cw), len = sizeof(Coefs<dw>); };
+
+// Copy the parts of an instance descriptor a kernel of arithmetic R reads, in 16-byte chunks issued by
+// the first threads of the block; completes at the issuing threads' next cp_async_wait_all.
+template <class S, class R>
+__device__ __forceinline__ void desc_copy_async(BatchInst<S>* dst, const BatchInst<S>* src) {
+  constexpr size_t HEAD = offsetof(DevParams, cd) / 16;                 // nx .. heat_unit_rates
+  constexpr size_t COEF = (CoefSpan<R>::len + 15) / 16;                  // the coefficient set
+  constexpr size_t TAIL_OFF = offsetof(BatchInst<S>, f);                 // pointers and step state
+  constexpr size_t TAIL = (sizeof(BatchInst<S>) - TAIL_OFF) / 16;
+  static_assert(offsetof(DevParams, cd) % 16 == 0 && CoefSpan<R>::off % 16 == 0 && TAIL_OFF % 16 == 0 &&
+                    sizeof(BatchInst<S>) % 16 == 0,
+                "descriptor parts must be 16-byte aligned");
+  static_assert(CoefSpan<R>::off + 16 * COEF <= sizeof(DevParams), "coefficient span inside the parameters");
+  const unsigned char* s = (const unsigned char*)src;
+  unsigned char* d = (unsigned char*)dst;
+  const int k = threadIdx.x;
+  if (k < (int)HEAD) {
+    cp_async16(d + 16 * k, s + 16 * k);
+  } else if (k < (int)(HEAD + COEF)) {
+    const size_t o = CoefSpan<R>::off + 16 * (k - HEAD);
+    cp_async16(d + o, s + o);
+  } else if (k < (int)(HEAD + COEF + TAIL)) {
+    const size_t o = TAIL_OFF + 16 * (k - HEAD - COEF);
+    cp_async16(d + o, s + o);
+  }
+}
+
 template <class S, class R, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY, sizeof(S) <= 4 ? 1024 / (TX * TY) : 1) k_batch_step(const BatchMeta* __restrict__ meta,
-                                                       const BatchInst<S>* __restrict__ insts) {
+__global__ void __launch_bounds__(TX* TY, sizeof(S) <= 4 ? 1024 / (TX * TY) : 1)
+    k_batch_step(const BatchMeta* __restrict__ meta, const BatchInst<S>* __restrict__ insts) {
+  static_assert(TX * TY >= 128, "the descriptor copy needs at least 128 threads");
+  static_assert(sizeof(BatchTile) == 16, "a work-list entry is one 16-byte copy");
   __shared__ FusedSmem<R, TX, TY> sm;
-  __shared__ DevParams sP;
+  __shared__ BatchInst<S> sI[2];
+  __shared__ BatchTile st[3];  // this tile's entry, the next one's, and the one after (filled while computing)
   const int ntiles = meta->ntiles;
   const BatchTile* __restrict__ tiles = meta->tiles;
-  int have = -1;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const BatchTile tile = tiles[t];
-    __syncthreads();  // the previous tile is done with the shared memory
-    if (tile.inst != have) {
-      const int* src = (const int*)&insts[tile.inst].P;
-      int* dst = (int*)&sP;
-      for (int k = threadIdx.x; k < (int)(sizeof(DevParams) / sizeof(int)); k += TX * TY) dst[k] = src[k];
-      have = tile.inst;
-      __syncthreads();
-    }
-    const BatchInst<S>& I = insts[tile.inst];
+  const int G = gridDim.x;
+  int t = blockIdx.x;
+  if (t >= ntiles) return;
+  if (threadIdx.x == 0) {
+    st[0] = tiles[t];
+    if (t + G < ntiles) st[1] = tiles[t + G];
+  }
+  __syncthreads();
+  desc_copy_async<S, R>(&sI[0], &insts[st[0].inst]);
+  cp_async_wait_all();
+  __syncthreads();
+  int slot = 0, r = 0;  // descriptor slot of this tile; ring position of this tile's entry
+  for (;;) {
+    const BatchTile tile = st[r];
+    const int rn = r == 2 ? 0 : r + 1, ra = rn == 2 ? 0 : rn + 1;
+    const bool more = t + G < ntiles;
+    const bool change = more && st[rn].inst != tile.inst;
+    if (change) desc_copy_async<S, R>(&sI[slot ^ 1], &insts[st[rn].inst]);
+    if (threadIdx.x == TX * TY - 1 && t + 2 * G < ntiles) cp_async16(&st[ra], &tiles[t + 2 * G]);
+    const BatchInst<S>& I = sI[slot];
+    const DevParams& P = I.P;
     const int cur = I.cur;
     const long long step = I.step;
-    const bool interior = tile.x0 >= 3 && tile.x0 + TX + 3 <= sP.nx && tile.y0 >= 3 && tile.y0 + TY + 3 <= sP.ny;
+    const bool interior = tile.x0 >= 3 && tile.x0 + TX + 3 <= P.nx && tile.y0 >= 3 && tile.y0 + TY + 3 <= P.ny;
     if (interior)
-      fused_body<true, S, R, TX, TY>(I.f[cur], I.g[cur], I.f[cur ^ 1], I.g[cur ^ 1], (R*)I.phi_prev, sP, step,
-                                     step == 0, I.scalars, I.partials, I.status, sm, tile.x0, tile.y0, tile.pslot);
+      fused_body<1, S, R, TX, TY>(I.f[cur], I.g[cur], I.f[cur ^ 1], I.g[cur ^ 1], (R*)I.phi_prev, P, step, step == 0,
+                                  I.scalars, I.partials, I.status, sm, tile.x0, tile.y0, tile.pslot);
     else
-      fused_body<false, S, R, TX, TY>(I.f[cur], I.g[cur], I.f[cur ^ 1], I.g[cur ^ 1], (R*)I.phi_prev, sP, step,
-                                      step == 0, I.scalars, I.partials, I.status, sm, tile.x0, tile.y0, tile.pslot);
+      fused_body<0, S, R, TX, TY>(I.f[cur], I.g[cur], I.f[cur ^ 1], I.g[cur ^ 1], (R*)I.phi_prev, P, step, step == 0,
+                                  I.scalars, I.partials, I.status, sm, tile.x0, tile.y0, tile.pslot);
+    cp_async_wait_all();
+    __syncthreads();  // the tile is done with the shared memory; the next descriptor and entry have landed
+    if (!more) break;
+    if (change) slot ^= 1;
+    t += G;
+    r = rn;
   }
 }
 

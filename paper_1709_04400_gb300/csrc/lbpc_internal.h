@@ -58,7 +58,7 @@ int split_block();
 
 // ---- batched step (lbpc_fused.cu kernels, lbpc_batch.cu host) ----
 // One instance of a batch as the device sees it; S is the storage type of the batch.
-template <class S> struct BatchInst {
+template <class S> struct alignas(16) BatchInst {
   DevParams P;
   PopBuf<S> f[2], g[2];
   void* phi_prev;      // arithmetic type
