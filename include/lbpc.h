@@ -238,14 +238,19 @@ lbpc_status lbpc_batch_sums(lbpc_batch* b, int32_t id, double* mass, double* hea
 /* Steps taken by instance id (-1 if no such instance). */
 int64_t lbpc_batch_step_count(const lbpc_batch* b, int32_t id);
 
-/* Tile shape (variant 0: 32x8, 1: 32x16, 2: 64x8) and persistent CTAs per SM of the step kernel. */
+/* Tile shape (variant 0: 32x8, 1: 32x16, 2: 64x8) and CTAs launched per SM of the step kernel. Each
+ * CTA walks the work list from its index in steps of the grid size. Up to the residency limit of the
+ * variant, every CTA is resident (a persistent grid). Above it, up to 64 times that limit, further
+ * CTAs start as earlier ones finish, so the hardware balances tiles of uneven cost. A value above
+ * that returns LBPC_EINVAL. */
 lbpc_status lbpc_batch_set_config(lbpc_batch* b, int32_t variant, int32_t ctas_per_sm);
 lbpc_status lbpc_batch_config(const lbpc_batch* b, int32_t* tile_x, int32_t* tile_y, int32_t* ctas_per_sm,
                               int32_t* graph_chunk);
 
-/* Time every tile shape and CTA count on the batch's own instances and keep the fastest. Every
- * configuration computes the same step, so tuning advances the batch by real steps: one warm-up
- * plus steps_per_candidate per candidate. */
+/* Time every tile shape with 1 .. residency-limit CTAs per SM and with 4, 8, 16, 32 and 64 times
+ * that limit on the batch's own instances, and keep the fastest. Every configuration computes the same
+ * step, so tuning advances the batch by real steps: one warm-up plus steps_per_candidate per
+ * candidate. */
 lbpc_status lbpc_batch_autotune(lbpc_batch* b, int32_t steps_per_candidate, int32_t* best_variant, int32_t* best_ctas,
                                 float* best_ms_per_step);
 

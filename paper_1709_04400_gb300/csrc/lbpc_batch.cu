@@ -532,7 +532,8 @@ LBPC_API lbpc_status lbpc_batch_set_config(lbpc_batch* b, int32_t variant, int32
   if (!b || variant < 0 || variant >= lbpc::kBatchVariants || ctas_per_sm < 1) return LBPC_EINVAL;
   DevGuard g(b->device);
   const int occ = lbpc::batch_max_ctas_per_sm(b->prec, variant);
-  if (ctas_per_sm > occ) return bfail(b, LBPC_EINVAL, "ctas_per_sm %d above the occupancy limit %d", ctas_per_sm, occ);
+  if (occ < 1 || ctas_per_sm > 64 * occ)
+    return bfail(b, LBPC_EINVAL, "ctas_per_sm %d above 64 times the residency limit %d", ctas_per_sm, occ);
   BCU(b, cudaStreamSynchronize(b->stream), "lbpc_batch_set_config sync");
   b->variant = variant;
   b->ctas = ctas_per_sm;
@@ -565,7 +566,10 @@ LBPC_API lbpc_status lbpc_batch_autotune(lbpc_batch* b, int32_t steps_per_candid
   int bv = b->variant, bc = b->ctas;
   for (int v = 0; v < lbpc::kBatchVariants; ++v) {
     const int occ = lbpc::batch_max_ctas_per_sm(b->prec, v);
-    for (int c = 1; c <= std::min(occ, 4); ++c) {
+    std::vector<int> cand;
+    for (int c = 1; c <= std::min(occ, 4); ++c) cand.push_back(c);  // persistent grids
+    for (int m : {4, 8, 16, 32, 64}) cand.push_back(m * occ);       // oversubscribed grids
+    for (int c : cand) {
       if (lbpc_batch_set_config(b, v, c) != LBPC_OK) continue;
       // every configuration computes the same step, so tuning advances the batch for real
       if (lbpc_batch_step(b, 1) != LBPC_OK) break;  // warm-up
