@@ -212,7 +212,9 @@ size_t lbpc_batch_instance_bytes(const lbpc_params* p);
 
 /* Create an empty batch of at most max_instances instances in storage precision prec (LBPC_FP64,
  * LBPC_FP32 or LBPC_FP16DEV; LBPC_DF64 returns LBPC_EINVAL) over the caller's arena (256-byte
- * aligned, bytes long). Fixed descriptors take a small part of the arena. */
+ * aligned, bytes long). Fixed descriptors take a small part of the arena. The initial configuration
+ * is 32 x 16 tiles with 16 times the residency limit of CTAs launched per SM (see
+ * lbpc_batch_set_config). */
 lbpc_status lbpc_batch_create(int32_t prec, int32_t max_instances, void* d_arena, size_t bytes, void* stream,
                               lbpc_batch** out);
 

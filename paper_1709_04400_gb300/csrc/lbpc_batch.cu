@@ -134,8 +134,8 @@ struct lbpc_batch {
   size_t tiles_off = 0, tiles_cap = 0;     // work list block (grows)
   std::vector<HostInst> inst;
   size_t inst_struct;  // sizeof(BatchInst<S>)
-  int variant = 0;     // tile shape
-  int ctas = 2;        // CTAs per SM of the persistent step kernel
+  int variant = 1;     // tile shape (32 x 16)
+  int ctas = 2;        // CTAs launched per SM by the step kernel (set at creation)
   int chunk = 16;      // steps per captured graph
   cudaGraphExec_t graph = nullptr;
   int graph_variant = -1, graph_ctas = -1, graph_ninst = -1;
@@ -361,8 +361,10 @@ LBPC_API lbpc_status lbpc_batch_create(int32_t prec, int32_t max_instances, void
       delete b;
       return LBPC_ECUDA;
     }
+    // default: 16 times the residency limit, the grid the autotuner picks or comes within a few per
+    // cent of on uneven instance mixes (the hardware balances tiles of uneven cost)
     const int occ = lbpc::batch_max_ctas_per_sm(prec, b->variant);
-    b->ctas = std::max(1, std::min(2, occ));
+    b->ctas = 16 * std::max(1, occ);
     if (rebuild(b) != LBPC_OK) {
       delete b;
       return LBPC_ECUDA;
