@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the double-word (DF64) variant of an FP64 run")
+    ap.add_argument("--no-side-run", action="store_true", help="served workload: no 4096^2 FP16 run alongside")
     return ap.parse_args()
 
 
@@ -181,6 +182,14 @@ def _dtypes():
     from paper_1709_04400_gb300 import lbpc
 
     return {lbpc.FP64: "f64", lbpc.DF64: "df64 (f32 pair)", lbpc.FP32: "f32", lbpc.FP16DEV: "f32 (f16 storage)"}
+
+
+def _peak_hbm():
+    """Measured copy bandwidth of the GB300s in GB/s (fallback 6800)."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
 
 
 def run_native(args):
@@ -465,10 +474,59 @@ def run_serve(args):
     reqs = serve.poisson_stream(args.requests, rate=args.rate, seed=170904400 + 4, side_lo=64, side_hi=512,
                                 steps_lo=1000, steps_hi=5000)
     srv = serve.Server(prec=prec, hbm_budget_bytes=24 << 30)
+
+    # the stream runs alongside one 4096 x 4096 FP16-deviation evaporation run on its own CUDA stream,
+    # stepped by a host thread (the library calls release the GIL), whose throughput measures the
+    # roofline under co-scheduling; its standalone rate is measured first for comparison
+    side = None
+    if not args.no_side_run:
+        import threading
+
+        from paper_1709_04400_gb300 import workloads
+
+        p0 = lbpc.Params(nx=8, ny=8)
+        Tc, _ = lbpc.eos_critical(p0)
+        rv, rl, _ = lbpc.coexistence(p0, 0.86 * Tc)
+        n4 = 4096
+        c4, r4, t4 = workloads.droplet_evaporation(Tc, rv, rl, n=n4, radius=0.2 * n4, dT_ratio=0.1)
+        s4 = torch.cuda.Stream()
+        big = lbpc.Simulation(lbpc.params_from_case(c4, lbpc.FP16DEV), stream=s4)
+        big.init(r4, t4)
+        big.step(5)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s4)
+        big.step(50)
+        e1.record(s4)
+        e1.synchronize()
+        alone_glups = n4 * n4 * 50 / e0.elapsed_time(e1) / 1e6
+        stop, done, err = threading.Event(), [0], []
+
+        def side_loop():
+            e0.record(s4)
+            try:
+                while not stop.is_set():
+                    big.step(20)
+                    done[0] += 20
+            except lbpc.LbpcError as e:
+                err.append(str(e))
+            e1.record(s4)
+            s4.synchronize()
+
+        th = threading.Thread(target=side_loop)
+        th.start()
     with ClockSampler(local) as clk:
         srv.run(reqs)
     st = srv.stats()
     srv.close()
+    if not args.no_side_run:
+        stop.set()
+        th.join()
+        big.close()
+        glups = n4 * n4 * done[0] / e0.elapsed_time(e1) / 1e6
+        side = {"workload": f"droplet_evaporation_{n4}_fp16dev", "steps": done[0], "glups_alongside": glups,
+                "glups_alone": alone_glups, "bytes_per_node": 96,
+                "hbm_frac_alongside": glups * 1e9 * 96 / 1e9 / _peak_hbm(), "hbm_frac_alone":
+                alone_glups * 1e9 * 96 / 1e9 / _peak_hbm(), "error": err[0] if err else None}
     if rank == 0:
         line = {"metric": "served coupled flow+thermal MLUPS (aggregate)", "value": st["aggregate_mlups"],
                 "unit": "MLUPS", "n_gpus": 1, "steps": None, "warmup": 0, "ms_per_step": None,
@@ -478,7 +536,7 @@ def run_serve(args):
                            "sides": [64, 512], "steps": [1000, 5000], "mix": "half evaporation, half heated wall",
                            "storage": args.prec or "fp32", "budget_gb": 24},
                 "latency": {"p50_s": st["p50_s"], "p99_s": st["p99_s"], "mean_s": st["mean_s"]},
-                "served": st, "clocks": clk.summary()}
+                "served": st, "side_run": side, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
 
 

@@ -94,3 +94,34 @@ def test_gong_cheng_divergence_matches_oracle():
     assert eg.value.status == lbpc.LBPC_ENONPHYS
     o = eo.value
     assert f"step {o.step}, node (x={o.x}, y={o.y})" in str(eg.value), (str(eo.value), str(eg.value))
+
+
+def test_heated_strip_nucleates_vapour():
+    """Sec. IV B, qualitatively: liquid over a wall at T_sat with a hotter strip (here the closed pool of
+    the heated-wall workload, strip T_s + 0.3 T_c). Vapour must form over the strip, on the wall, and
+    nowhere else along the wall, and the FP32 step must show the same vapour region as FP64. Neither
+    the contact-angle scheme nor the top boundary is named in the paper, so the departure diameter of
+    Fig. 7 is not compared."""
+    from scipy import ndimage
+
+    case, rho, T = workloads.heated_wall(TC, RV, RL, top="wall")
+    x0, x1, _ = case["strip"]
+    mid = 0.5 * (RV + RL)
+    areas = {}
+    for prec in (lbpc.FP64, lbpc.FP32):
+        sim = lbpc.Simulation(lbpc.params_from_case(case, prec))
+        sim.init(rho, T)
+        sim.step(1000)
+        r = sim.fields()[0]
+        sim.close()
+        ny = r.shape[0]
+        lab, n = ndimage.label(r[: ny // 2 - 20] < mid)  # vapour below the free surface
+        assert n >= 1, prec
+        sizes = ndimage.sum(np.ones_like(lab), lab, index=range(1, n + 1))
+        big = 1 + int(np.argmax(sizes))
+        ys, xs = np.nonzero(lab == big)
+        assert ys.min() == 0, "the vapour region sits on the wall"
+        assert x0 - 15 <= xs.min() and xs.max() < x1 + 15, (xs.min(), xs.max(), x0, x1)
+        assert r[1:6, : x0 - 40].min() > 0.9 * RL and r[1:6, x1 + 40:].min() > 0.9 * RL, "far wall stays liquid"
+        areas[prec] = sizes.max()
+    assert abs(areas[lbpc.FP32] - areas[lbpc.FP64]) <= 0.05 * areas[lbpc.FP64], areas
