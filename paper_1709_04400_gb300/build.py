@@ -39,7 +39,10 @@ def build(force=False, verbose=False, extra_flags=()):
     """Compile every CUDA source of the library into liblbpc.so next to this file."""
     if not force and up_to_date():
         return LIB
-    cmd = [nvcc_path(), *ARCH, "-lineinfo", "-O3", "-std=c++17", "--threads", "0",
+    # -prec-div=false -prec-sqrt=false: binary32 '/' and sqrtf take the approximate hardware forms
+    # (about 2 ulp; the FP32 path is held to 1e-4). Binary64 arithmetic and the double-word type's
+    # explicitly rounded intrinsics are not affected.
+    cmd = [nvcc_path(), *ARCH, "-lineinfo", "-O3", "-std=c++17", "--threads", "0", "-prec-div=false", "-prec-sqrt=false",
            "-Xcompiler", "-fPIC,-fvisibility=hidden", "-shared", "-I", os.path.join(ROOT, "include"),
            *extra_flags, "-o", LIB + ".tmp"] + [os.path.join(CSRC, f) for f in SOURCES]
     if verbose:
