@@ -12,7 +12,8 @@
 //   2Prod      p + e = a * b exactly, with one fused multiply-add
 // and the double-word algorithms analysed by Joldes, Muller and Popescu, "Tight and rigorous error
 // bounds for basic building blocks of double-word arithmetic", ACM TOMS 44(2), 2017:
-//   addition   their "sloppy" DW + DW: error below about 2^-47 (|x| + |y|), i.e. bounded relative to
+//   addition   TwoSum of the high words plus the low words, without the final renormalisation of
+//              their "sloppy" DW + DW: error below a few 2^-48 (|x| + |y|), i.e. bounded relative to
 //              the operands as binary64 rounding is, not relative to a cancelling result
 //   product    DW x DW with FMA (their DWTimesDW2): relative error below 5 * 2^-48
 //   division   binary32 quotient corrected once by the exactly computed remainder (Dekker 1971)
@@ -63,9 +64,16 @@ __device__ __forceinline__ dw dw_two_prod(float a, float b) {
   return dw(p, __fmaf_rn(a, b, -p));
 }
 
+// Renormalise a pair so that |lo| <= ulp(hi)/2 (TwoSum, exact for any hi, lo).
+__device__ __forceinline__ dw dw_norm(dw x) { return dw_two_sum(x.hi, x.lo); }
+
+// Addition without the final renormalisation: TwoSum of the high words plus the low words. The pair
+// it returns may have |lo| a few ulp(hi) (after cancellation, more); its absolute error, like that of
+// the normalised "sloppy" sum, stays within a few 2^-48 (|x| + |y|). Products take such pairs as they
+// are; division, roots, comparisons and checks renormalise first.
 __device__ __forceinline__ dw operator+(dw x, dw y) {
   const dw s = dw_two_sum(x.hi, y.hi);
-  return dw_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+  return dw(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
 }
 __device__ __forceinline__ dw operator-(dw x) { return dw(-x.hi, -x.lo); }
 __device__ __forceinline__ dw operator-(dw x, dw y) { return x + (-y); }
@@ -88,6 +96,8 @@ __device__ __forceinline__ dw operator*(float c, dw x) { return x * c; }
 __device__ __forceinline__ dw operator*(dw x, int c) { return x * (float)c; }  // |c| < 2^24
 
 __device__ __forceinline__ dw operator/(dw x, dw y) {
+  x = dw_norm(x);
+  y = dw_norm(y);
   const float r = __frcp_rn(y.hi);
   const float q1 = __fmul_rn(x.hi, r);
   // remainder x - q1 y: q1 y.hi exactly by 2Prod, q1 y.lo to binary32 precision
@@ -100,21 +110,33 @@ __device__ __forceinline__ dw& operator+=(dw& a, dw b) { return a = a + b; }
 __device__ __forceinline__ dw& operator-=(dw& a, dw b) { return a = a - b; }
 __device__ __forceinline__ dw& operator*=(dw& a, dw b) { return a = a * b; }
 
-__device__ __forceinline__ bool operator<(dw a, dw b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
-__device__ __forceinline__ bool operator>(dw a, dw b) { return b < a; }
-__device__ __forceinline__ bool operator<=(dw a, dw b) { return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo); }
-__device__ __forceinline__ bool operator>=(dw a, dw b) { return b <= a; }
+// comparisons of normalised pairs: the sign of the difference
+__device__ __forceinline__ bool dw_lt(dw a, dw b) {
+  a = dw_norm(a);
+  b = dw_norm(b);
+  return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+__device__ __forceinline__ bool dw_le(dw a, dw b) {
+  a = dw_norm(a);
+  b = dw_norm(b);
+  return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo);
+}
+__device__ __forceinline__ bool operator<(dw a, dw b) { return dw_lt(a, b); }
+__device__ __forceinline__ bool operator>(dw a, dw b) { return dw_lt(b, a); }
+__device__ __forceinline__ bool operator<=(dw a, dw b) { return dw_le(a, b); }
+__device__ __forceinline__ bool operator>=(dw a, dw b) { return dw_le(b, a); }
 
 __device__ __forceinline__ bool isfinite(dw a) { return ::isfinite(a.hi) && ::isfinite(a.lo); }
 
 // larger of a and b; a NaN operand yields the other one, as fmax does
 __device__ __forceinline__ dw fmax(dw a, dw b) {
-  if (::isnan(a.hi)) return b;
-  if (::isnan(b.hi)) return a;
-  return a < b ? b : a;
+  if (::isnan(a.hi) || ::isnan(a.lo)) return b;
+  if (::isnan(b.hi) || ::isnan(b.lo)) return a;
+  return a < b ? dw_norm(b) : dw_norm(a);
 }
 
 __device__ __forceinline__ dw sqrt(dw x) {
+  x = dw_norm(x);
   if (!(x.hi > 0.0f)) return dw(::sqrtf(x.hi), 0.0f);  // zero, negative (NaN) or NaN
   const float s = __fsqrt_rn(x.hi);
   const dw p = dw_two_prod(s, s);
@@ -123,9 +145,10 @@ __device__ __forceinline__ dw sqrt(dw x) {
 }
 
 __device__ __forceinline__ dw rsqrt(dw x) {
+  x = dw_norm(x);
   const float r = __frcp_rn(__fsqrt_rn(x.hi));
-  const dw e = dw(1) - x * dw_two_prod(r, r);  // 1 - x r^2, small
-  return dw_fast_two_sum(r, __fmul_rn(__fmul_rn(0.5f, r), e.hi));
+  const dw e = dw(1) - x * dw_two_prod(r, r);  // 1 - x r^2, small; both words count (e is not normalised)
+  return dw_fast_two_sum(r, __fmul_rn(__fmul_rn(0.5f, r), __fadd_rn(e.hi, e.lo)));
 }
 
 // read-only load of a plane value in any arithmetic type
