@@ -178,6 +178,29 @@ lbpc_status lbpc_fields(lbpc_ctx* c, double* rho, double* ux, double* uy, double
  * fixed order. Synchronises the stream. */
 lbpc_status lbpc_sums(lbpc_ctx* c, double* mass, double* heat);
 
+/* Checkpoint / resume. The paper has no counterpart; this is plumbing for long runs and for a
+ * service that moves or pre-empts simulations.
+ *
+ * A checkpoint is the context's whole state in raw form:
+ *   - a 512-byte header: magic, version, the lbpc_params, the step counter and the lagged rho_ave;
+ *   - the current post-collision populations f and g in the storage type, plus the FP16 reference
+ *     planes for LBPC_FP16DEV;
+ *   - phi of the previous step, in the arithmetic type.
+ * Stepping a context restored from a checkpoint taken after k steps reproduces, bit for bit, the
+ * steps after k of an uninterrupted run with the same parameters and precision.
+ *
+ * lbpc_checkpoint_bytes: size of a checkpoint of this context (0 for a null context).
+ * lbpc_save: writes it into buf (host memory, or device memory when on_device is nonzero), which is
+ *   at least lbpc_checkpoint_bytes long and owned by the caller. The context must be initialised
+ *   and free of errors (LBPC_ESTATE otherwise). LBPC_EINVAL if buf is too small. Synchronises the
+ *   stream.
+ * lbpc_load: replaces the state of a context created with the same lbpc_params (compared byte for
+ *   byte; LBPC_EINVAL otherwise, and for a buffer that is not a checkpoint). The context need not
+ *   be initialised. Clears the non-physical status. Synchronises the stream. */
+size_t lbpc_checkpoint_bytes(const lbpc_ctx* c);
+lbpc_status lbpc_save(lbpc_ctx* c, void* buf, size_t bytes, int on_device);
+lbpc_status lbpc_load(lbpc_ctx* c, const void* buf, size_t bytes, int on_device);
+
 /* Raw populations of the current state in post-stream, post-boundary form: f, g are [9][ny][nx]
  * FP64 (D2Q9 order e0=(0,0), e1=(1,0), e2=(0,1), e3=(-1,0), e4=(0,-1), e5=(1,1), e6=(-1,1),
  * e7=(-1,-1), e8=(1,-1)). Either pointer may be NULL. Synchronises the stream. */

@@ -529,6 +529,124 @@ LBPC_API lbpc_status lbpc_fields(lbpc_ctx* c, double* rho, double* ux, double* u
   return LBPC_OK;
 }
 
+// ---- checkpoint / resume ----
+// Layout: a 512-byte header, then f and g of the current state (storage type, [9][N] each), the FP16
+// reference planes of f and g (FP16 storage only), and phi_prev ([N] of the arithmetic type).
+namespace {
+constexpr char kCkptMagic[8] = {'L', 'B', 'P', 'C', 'C', 'K', 'P', '1'};
+constexpr size_t kCkptHeader = 512;
+struct CkptHeader {
+  char magic[8];
+  uint32_t version, header_bytes;
+  lbpc_params params;  // no padding inside the struct: compared bytewise on load
+  int64_t step;
+  double rho_ave;
+  uint64_t pop_bytes, ref_bytes, phi_bytes;
+};
+static_assert(sizeof(CkptHeader) <= kCkptHeader, "checkpoint header fits its slot");
+static_assert(sizeof(lbpc_params) == 16 * 4 + 39 * 8, "lbpc_params has no padding");
+
+void ckpt_sizes(const lbpc_ctx* c, size_t& pop, size_t& ref, size_t& phi) {
+  const Layout L = layout_of(&c->p);
+  pop = 9 * (size_t)L.N * L.store;
+  ref = c->p.prec == LBPC_FP16DEV ? (size_t)L.N * sizeof(float) : 0;
+  phi = (size_t)L.N * L.real;
+}
+}  // namespace
+
+LBPC_API size_t lbpc_checkpoint_bytes(const lbpc_ctx* c) {
+  if (!c) return 0;
+  size_t pop, ref, phi;
+  ckpt_sizes(c, pop, ref, phi);
+  return kCkptHeader + 2 * pop + 2 * ref + phi;
+}
+
+LBPC_API lbpc_status lbpc_save(lbpc_ctx* c, void* buf, size_t bytes, int on_device) {
+  if (!c || !buf) return LBPC_EINVAL;
+  if (c->err != LBPC_OK) return LBPC_ESTATE;
+  if (!c->initialised) return fail(c, LBPC_ESTATE, "lbpc_save before lbpc_init");
+  if (bytes < lbpc_checkpoint_bytes(c)) return LBPC_EINVAL;
+  DeviceGuard g(c->device);
+  size_t pop, ref, phi;
+  ckpt_sizes(c, pop, ref, phi);
+  CkptHeader h{};
+  memcpy(h.magic, kCkptMagic, sizeof h.magic);
+  h.version = 1;
+  h.header_bytes = (uint32_t)kCkptHeader;
+  h.params = c->p;
+  h.step = c->step;
+  h.pop_bytes = pop;
+  h.ref_bytes = ref;
+  h.phi_bytes = phi;
+  CU(c, cudaMemcpyAsync(&h.rho_ave, c->buf.scalars, sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+     "lbpc_save rho_ave");
+  CU(c, cudaStreamSynchronize(c->stream), "lbpc_save sync");
+  unsigned char header[kCkptHeader] = {};
+  memcpy(header, &h, sizeof h);
+  unsigned char* dst = (unsigned char*)buf;
+  const cudaMemcpyKind d2x = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CU(c, cudaMemcpyAsync(dst, header, kCkptHeader, on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost,
+                        c->stream),
+     "lbpc_save header");
+  size_t off = kCkptHeader;
+  CU(c, cudaMemcpyAsync(dst + off, c->buf.f[c->cur], pop, d2x, c->stream), "lbpc_save f");
+  off += pop;
+  CU(c, cudaMemcpyAsync(dst + off, c->buf.g[c->cur], pop, d2x, c->stream), "lbpc_save g");
+  off += pop;
+  if (ref) {
+    CU(c, cudaMemcpyAsync(dst + off, c->buf.ref_f[c->cur], ref, d2x, c->stream), "lbpc_save ref_f");
+    off += ref;
+    CU(c, cudaMemcpyAsync(dst + off, c->buf.ref_g[c->cur], ref, d2x, c->stream), "lbpc_save ref_g");
+    off += ref;
+  }
+  CU(c, cudaMemcpyAsync(dst + off, c->buf.phi_prev, phi, d2x, c->stream), "lbpc_save phi_prev");
+  CU(c, cudaStreamSynchronize(c->stream), "lbpc_save sync");
+  return LBPC_OK;
+}
+
+LBPC_API lbpc_status lbpc_load(lbpc_ctx* c, const void* buf, size_t bytes, int on_device) {
+  if (!c || !buf) return LBPC_EINVAL;
+  if (c->err != LBPC_OK) return LBPC_ESTATE;
+  if (bytes < lbpc_checkpoint_bytes(c)) return fail(c, LBPC_EINVAL, "lbpc_load: checkpoint smaller than expected");
+  DeviceGuard g(c->device);
+  const unsigned char* src = (const unsigned char*)buf;
+  CkptHeader h{};
+  if (on_device) {
+    CU(c, cudaMemcpy(&h, src, sizeof h, cudaMemcpyDeviceToHost), "lbpc_load header");
+  } else {
+    memcpy(&h, src, sizeof h);
+  }
+  size_t pop, ref, phi;
+  ckpt_sizes(c, pop, ref, phi);
+  if (memcmp(h.magic, kCkptMagic, sizeof h.magic) != 0 || h.version != 1 || h.header_bytes != kCkptHeader)
+    return fail(c, LBPC_EINVAL, "lbpc_load: not a liblbpc checkpoint");
+  if (memcmp(&h.params, &c->p, sizeof(lbpc_params)) != 0)
+    return fail(c, LBPC_EINVAL, "lbpc_load: the checkpoint was taken with other parameters");
+  if (h.pop_bytes != pop || h.ref_bytes != ref || h.phi_bytes != phi || h.step < 0)
+    return fail(c, LBPC_EINVAL, "lbpc_load: section sizes do not match");
+  const cudaMemcpyKind x2d = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  size_t off = kCkptHeader;
+  CU(c, cudaMemcpyAsync(c->buf.f[0], src + off, pop, x2d, c->stream), "lbpc_load f");
+  off += pop;
+  CU(c, cudaMemcpyAsync(c->buf.g[0], src + off, pop, x2d, c->stream), "lbpc_load g");
+  off += pop;
+  if (ref) {
+    CU(c, cudaMemcpyAsync(c->buf.ref_f[0], src + off, ref, x2d, c->stream), "lbpc_load ref_f");
+    off += ref;
+    CU(c, cudaMemcpyAsync(c->buf.ref_g[0], src + off, ref, x2d, c->stream), "lbpc_load ref_g");
+    off += ref;
+  }
+  CU(c, cudaMemcpyAsync(c->buf.phi_prev, src + off, phi, x2d, c->stream), "lbpc_load phi_prev");
+  CU(c, cudaMemcpyAsync(c->buf.scalars, &h.rho_ave, sizeof(double), cudaMemcpyHostToDevice, c->stream),
+     "lbpc_load rho_ave");
+  CU(c, cudaMemsetAsync(c->buf.status, 0, 8 * sizeof(long long), c->stream), "lbpc_load status reset");
+  CU(c, cudaStreamSynchronize(c->stream), "lbpc_load sync");
+  c->cur = 0;
+  c->step = h.step;
+  c->initialised = 1;
+  return LBPC_OK;
+}
+
 LBPC_API lbpc_status lbpc_sums(lbpc_ctx* c, double* mass, double* heat) {
   if (!c) return LBPC_EINVAL;
   if (!c->initialised) return LBPC_ESTATE;

@@ -33,7 +33,7 @@ EXPORTED = ["lbpc_version", "lbpc_check_params", "lbpc_workspace_bytes", "lbpc_e
             "lbpc_batch_add", "lbpc_batch_remove", "lbpc_batch_step", "lbpc_batch_check", "lbpc_batch_fields",
             "lbpc_batch_sums", "lbpc_batch_step_count", "lbpc_batch_set_config", "lbpc_batch_config",
             "lbpc_batch_autotune", "lbpc_batch_free_bytes", "lbpc_batch_last_error", "lbpc_batch_destroy",
-            "lbpc_set_fused_tile"]
+            "lbpc_set_fused_tile", "lbpc_checkpoint_bytes", "lbpc_save", "lbpc_load"]
 
 
 class LbpcError(RuntimeError):
@@ -94,6 +94,9 @@ def load_library(path: str = LIB_PATH):
         "lbpc_kernel_name": (ctypes.c_char_p, [vp, ctypes.c_int32]),
         "lbpc_set_path": (ctypes.c_int, [vp, ctypes.c_int32]),
         "lbpc_set_fused_tile": (ctypes.c_int, [vp, ctypes.c_int32]),
+        "lbpc_checkpoint_bytes": (ctypes.c_size_t, [vp]),
+        "lbpc_save": (ctypes.c_int, [vp, vp, ctypes.c_size_t, ctypes.c_int]),
+        "lbpc_load": (ctypes.c_int, [vp, vp, ctypes.c_size_t, ctypes.c_int]),
         "lbpc_step_static": (ctypes.c_int, [P, vp, vp, vp, vp, vp, vp, ctypes.c_int64, vp]),
         "lbpc_batch_instance_bytes": (ctypes.c_size_t, [P]),
         "lbpc_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]),
@@ -307,6 +310,28 @@ class Simulation:
         m, h = ctypes.c_double(), ctypes.c_double()
         self._raise(self.lib.lbpc_sums(self.ctx, ctypes.byref(m), ctypes.byref(h)), "lbpc_sums")
         return m.value, h.value
+
+    def save(self, out=None):
+        """Checkpoint of the whole state (lbpc_save) into a host numpy uint8 array or, when out is a
+        CUDA uint8 tensor of at least checkpoint_bytes(), into it; returns the buffer."""
+        n = self.lib.lbpc_checkpoint_bytes(self.ctx)
+        if out is None:
+            out = np.empty(n, dtype=np.uint8)
+        dev = not isinstance(out, np.ndarray)
+        self._raise(self.lib.lbpc_save(self.ctx, _ptr(out), int(out.numel() if dev else out.size), int(dev)),
+                    "lbpc_save")
+        return out
+
+    def load(self, buf):
+        """Restore a checkpoint (lbpc_load) from a host numpy uint8 array or a CUDA uint8 tensor."""
+        dev = not isinstance(buf, np.ndarray)
+        if not dev:
+            buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        self._raise(self.lib.lbpc_load(self.ctx, _ptr(buf), int(buf.numel() if dev else buf.size), int(dev)),
+                    "lbpc_load")
+
+    def checkpoint_bytes(self):
+        return int(self.lib.lbpc_checkpoint_bytes(self.ctx))
 
     def populations(self):
         f = np.empty((9, self.ny, self.nx))

@@ -37,7 +37,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_struct_layout_matches_header():
-    # 16 int32 then 40 doubles: no padding, 384 bytes
+    # 16 int32 then 39 doubles: no padding, 376 bytes
     assert ctypes.sizeof(lbpc.CParams) == 16 * 4 + (5 + 9 + 9 + 4 + 2 + 4 + 4 + 2) * 8
     assert lbpc.CParams.a.offset == 64
 
