@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--dT", type=float, default=0.1, help="superheat dT / T_c of the evaporation case")
     ap.add_argument("--prec", default="", choices=["", "fp64", "df64", "fp32", "fp16"])
     ap.add_argument("--path", default="auto", choices=["auto", "split", "fused"])
-    ap.add_argument("--tile", type=int, default=0, help="fused tile shape: 0 = 32x16, 1 = 32x8")
+    ap.add_argument("--tile", type=int, default=0,
+                    help="fused tile: 0 = 32x16, 1 = 32x8, 2 = 32x16 two nodes per thread, 3 = 32x32 two per thread")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the double-word (DF64) variant of an FP64 run")

@@ -163,8 +163,10 @@ const char* lbpc_kernel_name(const lbpc_ctx* c, int32_t k);
 typedef enum { LBPC_PATH_AUTO = 0, LBPC_PATH_SPLIT = 1, LBPC_PATH_FUSED = 2 } lbpc_path;
 lbpc_status lbpc_set_path(lbpc_ctx* c, int32_t path);
 
-/* Tile shape of the fused step: 0 = 32 x 16 (default), 1 = 32 x 8 (smaller shared-memory footprint,
- * more resident CTAs per SM, more halo recomputation). Both compute the same step. */
+/* Tile configuration of the fused step (LBPC_FP32 and LBPC_FP16DEV): 0 = 32 x 16 tiles, one node per
+ * thread (default); 1 = 32 x 8, one node per thread (smaller shared-memory footprint, more halo
+ * recomputation); 2 = 32 x 16, two nodes per thread; 3 = 32 x 32, two nodes per thread (less halo
+ * recomputation per node). All compute the same step. LBPC_EINVAL outside 0..3. */
 lbpc_status lbpc_set_fused_tile(lbpc_ctx* c, int32_t tile);
 
 /* Synchronise the stream and check the device status word. */
@@ -263,7 +265,8 @@ lbpc_status lbpc_batch_sums(lbpc_batch* b, int32_t id, double* mass, double* hea
 /* Steps taken by instance id (-1 if no such instance). */
 int64_t lbpc_batch_step_count(const lbpc_batch* b, int32_t id);
 
-/* Tile shape (variant 0: 32x8, 1: 32x16, 2: 64x8) and CTAs launched per SM of the step kernel. Each
+/* Step-kernel variant and CTAs launched per SM. Variants: 0 = 32x8, 1 = 32x16, 2 = 64x8 tiles with one
+ * node per thread; 3 = 32x16, 4 = 64x16, 5 = 32x32 tiles with two nodes per thread. Each
  * CTA walks the work list from its index in steps of the grid size. Up to the residency limit of the
  * variant, every CTA is resident (a persistent grid). Above it, up to 64 times that limit, further
  * CTAs start as earlier ones finish, so the hardware balances tiles of uneven cost. A value above
@@ -272,8 +275,8 @@ lbpc_status lbpc_batch_set_config(lbpc_batch* b, int32_t variant, int32_t ctas_p
 lbpc_status lbpc_batch_config(const lbpc_batch* b, int32_t* tile_x, int32_t* tile_y, int32_t* ctas_per_sm,
                               int32_t* graph_chunk);
 
-/* Time every tile shape with 1 .. residency-limit CTAs per SM and with 4, 8, 16, 32 and 64 times
- * that limit on the batch's own instances, and keep the fastest. Every configuration computes the same
+/* Time every variant (tile shape and nodes per thread) with 1 .. residency-limit CTAs per SM and
+ * with 4, 8, 16, 32 and 64 times that limit on the batch's own instances, and keep the fastest. Every configuration computes the same
  * step, so tuning advances the batch by real steps: one warm-up plus steps_per_candidate per
  * candidate. */
 lbpc_status lbpc_batch_autotune(lbpc_batch* b, int32_t steps_per_candidate, int32_t* best_variant, int32_t* best_ctas,

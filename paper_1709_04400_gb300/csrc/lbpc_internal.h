@@ -37,7 +37,7 @@ struct SplitBuffers {
   double* scalars;   // [0] rho_ave, [1] mass, [2] heat
   long long* status; // [0] flag, [1] step, [2] x, [3] y, [4] code
   const TmaMaps* tma[2] = {nullptr, nullptr};  // tensor maps of buffer A / B for the TMA-staged fused step
-  int fused_tile = 0;                            // 0: 32 x 16 tiles, 1: 32 x 8 tiles (tensor maps must match)
+  int fused_tile = 0;  // 0: 32x16, 1: 32x8, 2: 32x16 two nodes per thread, 3: 32x32 two per thread (maps match)
 };
 
 // ev: null, or split_kernel_count(P) + 1 events recorded before the first and after each kernel.
@@ -79,12 +79,16 @@ struct BatchMeta {
   int ntiles;
   int ninst;  // instance slots (active or not)
 };
-// Tile shapes a batch can run with: 0 = 32x8, 1 = 32x16, 2 = 64x8.
-constexpr int kBatchVariants = 3;
+// Step-kernel variants of a batch (tile shape and nodes per thread): 0 = 32x8, 1 = 32x16, 2 = 64x8
+// with one node per thread; 3 = 32x16, 4 = 64x16, 5 = 32x32 with two nodes per thread.
+constexpr int kBatchVariants = 6;
 inline void batch_tile_shape(int v, int& tx, int& ty) {
-  tx = v == 2 ? 64 : 32;
-  ty = v == 1 ? 16 : 8;
+  static const int TXS[kBatchVariants] = {32, 32, 64, 32, 64, 32}, TYS[kBatchVariants] = {8, 16, 8, 16, 16, 32};
+  const int k = (v >= 0 && v < kBatchVariants) ? v : 0;
+  tx = TXS[k];
+  ty = TYS[k];
 }
+inline int batch_nodes_per_thread(int v) { return v >= 3 && v < kBatchVariants ? 2 : 1; }
 // Enqueue one batched step (persistent step kernel + per-instance advance) on st.
 cudaError_t batch_step_launch(int prec, int variant, int ctas, const BatchMeta* d_meta, void* d_insts, int ninst,
                               cudaStream_t st);

@@ -249,19 +249,24 @@ def test_fp16_deviation_storage(path):
 
 @pytest.mark.parametrize("prec", [lbpc.FP32, lbpc.FP16DEV], ids=["fp32", "fp16"])
 def test_fused_tile_shapes(prec):
-    """Both tile shapes of the fused step (32 x 16 and 32 x 8, TMA-staged interior tiles) compute the
-    same step; the FP32 result stays within 1e-4 of the oracle."""
-    case, rho, T = workloads.droplet_periodic(TC, RV, RL)
-    out = []
-    for tile in (0, 1):
-        sim = lbpc.Simulation(lbpc.params_from_case(case, prec))
-        sim.set_fused_tile(tile)
-        sim.init(rho, T)
-        sim.step(60)
-        out.append(sim.fields())
-        sim.close()
-    for a, b in zip(out[0], out[1]):
-        assert np.max(np.abs(a - b)) <= 1e-5 * np.max(np.abs(b)) + 1e-12
-    if prec == lbpc.FP32:
-        p, s = run_oracle(case, rho, T, 60)
-        _assert_within(_errors(out[1], p, s), 1e-4)
+    """Every tile configuration of the fused step (32 x 16 and 32 x 8 with one node per thread, 32 x 16
+    and 32 x 32 with two; TMA-staged interior tiles) computes the same step; the FP32 result stays
+    within 1e-4 of the oracle. A ragged 101 x 75 grid exercises partial tiles and the plain-load path
+    (its rows are not 16-byte multiples, so no TMA)."""
+    for case, rho, T in (workloads.droplet_periodic(TC, RV, RL), workloads.mixed_small(TC, RV, RL, nx=101, ny=75)):
+        out = []
+        for tile in (0, 1, 2, 3):
+            sim = lbpc.Simulation(lbpc.params_from_case(case, prec))
+            sim.set_fused_tile(tile)
+            sim.init(rho, T)
+            sim.step(60)
+            out.append(sim.fields())
+            sim.close()
+        for other in out[1:]:
+            for a, b in zip(other, out[0]):
+                # binary32 round-off of differently ordered operations, grown over 60 steps
+                assert np.max(np.abs(a - b)) <= 5e-5 * np.max(np.abs(b)) + 1e-12, case["name"]
+        if prec == lbpc.FP32:
+            p, s = run_oracle(case, rho, T, 60)
+            for o in out:
+                _assert_within(_errors(o, p, s), 1e-4)
