@@ -368,6 +368,7 @@ static char* dead_half(lbpc_ctx* c) { return (char*)c->buf.f[c->cur ^ 1]; }
 
 LBPC_API lbpc_status lbpc_init(lbpc_ctx* c, const double* rho, const double* T, const double* ux, const double* uy,
                                int on_device) {
+  lbpc::TraceRange trace_("lbpc_init");
   if (!c) return LBPC_EINVAL;
   if (c->err != LBPC_OK) return LBPC_ESTATE;
   if (!rho || !T) return fail(c, LBPC_EINVAL, "lbpc_init: rho and T are required");
@@ -437,6 +438,7 @@ LBPC_API lbpc_status lbpc_set_fused_tile(lbpc_ctx* c, int32_t tile) {
 }
 
 LBPC_API lbpc_status lbpc_step_async(lbpc_ctx* c, int64_t n) {
+  lbpc::TraceRange trace_("lbpc_step_async");
   if (!c || n < 0) return LBPC_EINVAL;
   if (c->err != LBPC_OK) return LBPC_ESTATE;
   if (!c->initialised) return fail(c, LBPC_ESTATE, "lbpc_step before lbpc_init");
@@ -480,6 +482,7 @@ LBPC_API lbpc_status lbpc_step(lbpc_ctx* c, int64_t n) {
 }
 
 LBPC_API lbpc_status lbpc_step_timed(lbpc_ctx* c, float* kernel_ms, int32_t max_kernels, int32_t* n_kernels) {
+  lbpc::TraceRange trace_("lbpc_step_timed");
   if (!c || (max_kernels > 0 && !kernel_ms)) return LBPC_EINVAL;
   if (c->err != LBPC_OK) return LBPC_ESTATE;
   if (!c->initialised) return fail(c, LBPC_ESTATE, "lbpc_step_timed before lbpc_init");
@@ -508,6 +511,7 @@ LBPC_API const char* lbpc_kernel_name(const lbpc_ctx* c, int32_t k) {
 }
 
 LBPC_API lbpc_status lbpc_fields(lbpc_ctx* c, double* rho, double* ux, double* uy, double* T, int on_device) {
+  lbpc::TraceRange trace_("lbpc_fields");
   if (!c) return LBPC_EINVAL;
   if (!c->initialised) return LBPC_ESTATE;
   DeviceGuard g(c->device);
@@ -562,6 +566,7 @@ LBPC_API size_t lbpc_checkpoint_bytes(const lbpc_ctx* c) {
 }
 
 LBPC_API lbpc_status lbpc_save(lbpc_ctx* c, void* buf, size_t bytes, int on_device) {
+  lbpc::TraceRange trace_("lbpc_save");
   if (!c || !buf) return LBPC_EINVAL;
   if (c->err != LBPC_OK) return LBPC_ESTATE;
   if (!c->initialised) return fail(c, LBPC_ESTATE, "lbpc_save before lbpc_init");
@@ -605,6 +610,7 @@ LBPC_API lbpc_status lbpc_save(lbpc_ctx* c, void* buf, size_t bytes, int on_devi
 }
 
 LBPC_API lbpc_status lbpc_load(lbpc_ctx* c, const void* buf, size_t bytes, int on_device) {
+  lbpc::TraceRange trace_("lbpc_load");
   if (!c || !buf) return LBPC_EINVAL;
   if (c->err != LBPC_OK) return LBPC_ESTATE;
   if (bytes < lbpc_checkpoint_bytes(c)) return fail(c, LBPC_EINVAL, "lbpc_load: checkpoint smaller than expected");
@@ -648,6 +654,7 @@ LBPC_API lbpc_status lbpc_load(lbpc_ctx* c, const void* buf, size_t bytes, int o
 }
 
 LBPC_API lbpc_status lbpc_sums(lbpc_ctx* c, double* mass, double* heat) {
+  lbpc::TraceRange trace_("lbpc_sums");
   if (!c) return LBPC_EINVAL;
   if (!c->initialised) return LBPC_ESTATE;
   DeviceGuard g(c->device);
@@ -661,6 +668,7 @@ LBPC_API lbpc_status lbpc_sums(lbpc_ctx* c, double* mass, double* heat) {
 }
 
 LBPC_API lbpc_status lbpc_populations(lbpc_ctx* c, double* f, double* g, int on_device) {
+  lbpc::TraceRange trace_("lbpc_populations");
   if (!c) return LBPC_EINVAL;
   if (!c->initialised) return LBPC_ESTATE;
   DeviceGuard dg(c->device);

@@ -376,6 +376,7 @@ LBPC_API lbpc_status lbpc_batch_create(int32_t prec, int32_t max_instances, void
 
 LBPC_API lbpc_status lbpc_batch_add(lbpc_batch* b, const lbpc_params* p, const double* rho, const double* T,
                                     int on_device, int32_t* id) {
+  lbpc::TraceRange trace_("lbpc_batch_add");
   if (!b || !p || !rho || !T) return LBPC_EINVAL;
   if (b->err != LBPC_OK) return LBPC_ESTATE;
   char why[256];
@@ -438,6 +439,7 @@ LBPC_API lbpc_status lbpc_batch_remove(lbpc_batch* b, int32_t id) {
 }
 
 LBPC_API lbpc_status lbpc_batch_step(lbpc_batch* b, int64_t n) {
+  lbpc::TraceRange trace_("lbpc_batch_step");
   if (!b || n < 0) return LBPC_EINVAL;
   if (b->err != LBPC_OK) return LBPC_ESTATE;
   DevGuard g(b->device);
@@ -485,6 +487,7 @@ LBPC_API lbpc_status lbpc_batch_check(lbpc_batch* b, int32_t* failed_id) {
 
 LBPC_API lbpc_status lbpc_batch_fields(lbpc_batch* b, int32_t id, double* rho, double* ux, double* uy, double* T,
                                        int on_device) {
+  lbpc::TraceRange trace_("lbpc_batch_fields");
   if (!b || id < 0 || id >= (int)b->inst.size() || !b->inst[id].used) return LBPC_EINVAL;
   DevGuard g(b->device);
   HostInst& h = b->inst[id];
@@ -557,6 +560,7 @@ LBPC_API lbpc_status lbpc_batch_config(const lbpc_batch* b, int32_t* tile_x, int
 
 LBPC_API lbpc_status lbpc_batch_autotune(lbpc_batch* b, int32_t steps_per_candidate, int32_t* best_variant,
                                          int32_t* best_ctas, float* best_ms_per_step) {
+  lbpc::TraceRange trace_("lbpc_batch_autotune");
   if (!b || steps_per_candidate < 1) return LBPC_EINVAL;
   if (b->err != LBPC_OK) return LBPC_ESTATE;
   if (active_count(b) == 0) return bfail(b, LBPC_EINVAL, "lbpc_batch_autotune: the batch is empty");

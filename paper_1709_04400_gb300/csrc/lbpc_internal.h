@@ -4,9 +4,20 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lbpc_device.cuh"
 
 namespace lbpc {
+
+// NVTX range over a host call of the library (NVTX v3 is header-only: without an attached profiler a
+// range costs a check of a null function pointer). Profilers show and filter by these names.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 template <class S, int TX, int TY> struct TmaBox {
   static constexpr int XOFF = 16 / (int)sizeof(S) > 4 ? 16 / (int)sizeof(S) : 4;
