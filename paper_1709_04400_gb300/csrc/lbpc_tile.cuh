@@ -163,6 +163,7 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
   // ---- stage 1a: own nodes (kept in registers) ----
   R f[NPT][9], g[NPT][9];
   R rho[NPT], T[NPT], dpdT[NPT];
+  R pp[NPT];  // phi of the previous step, loaded here so that the load overlaps stages 1-2
   int my[NPT];
   bool active[NPT];
 #pragma unroll
@@ -171,6 +172,7 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
     const int tx = n % TX, ty = n / TX;
     const int gx = x0 + tx, gy = y0 + ty;
     active[k] = gx < P.nx && gy < P.ny;
+    pp[k] = (active[k] && P.model == 0 && !first) ? phi_prev[(long long)gy * P.nx + gx] : R(0);
     const int mx = wrap_any(gx, P.nx);
     my[k] = row_of(P, gy);
     if (MODE == 2) {
@@ -360,10 +362,7 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
     } else {
       phi = div_lam_gradT * inv_rcv - C.kdiff * lapT + compress;
       S0 = phi;
-      if (P.model == 0) {
-        const R pp = first ? phi : phi_prev[i];
-        S0 = phi + (phi - pp) * 0.5f;
-      }
+      if (P.model == 0) S0 = phi + (phi - (first ? phi : pp[k])) * 0.5f;
     }
     phi_prev[i] = phi;
     collide_flow(f[k], rho[k], vx[k], vy[k], Fx[k], Fy[k], Q[k], P);
