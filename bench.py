@@ -44,8 +44,9 @@ def parse():
     ap.add_argument("--dT", type=float, default=0.1, help="superheat dT / T_c of the evaporation case")
     ap.add_argument("--prec", default="", choices=["", "fp64", "df64", "fp32", "fp16"])
     ap.add_argument("--path", default="auto", choices=["auto", "split", "fused"])
-    ap.add_argument("--tile", type=int, default=0,
-                    help="fused tile: 0 = 32x16, 1 = 32x8, 2 = 32x16 two nodes per thread, 3 = 32x32 two per thread")
+    ap.add_argument("--tile", type=int, default=-1,
+                    help="fused tile: -1 = library default (32x8), 0 = 32x16, 1 = 32x8, 2 = 32x16 two nodes "
+                         "per thread, 3 = 32x32 two per thread")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the double-word (DF64) variant of an FP64 run")
@@ -221,7 +222,8 @@ def run_native(args):
     path = {"auto": lbpc.PATH_AUTO, "split": lbpc.PATH_SPLIT, "fused": lbpc.PATH_FUSED}[args.path]
     sim = lbpc.Simulation(params)
     sim.set_path(path)
-    sim.set_fused_tile(args.tile)
+    if args.tile >= 0:
+        sim.set_fused_tile(args.tile)
     sim.init(rho, T)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     stream = sim.stream
@@ -362,6 +364,7 @@ def run_native(args):
             "dtype": DTYPE[prec], "data": "synthetic",
             "config": {"workload": case["name"], "nx": case["nx"], "ny": case["ny"], "nodes": N,
                        "storage": prec_name, "parallelism": f"replicas{ws}", "path": args.path,
+                       "fused_tile": args.tile if args.tile >= 0 else "library default (32x8)",
                        "l2": "flushed before every timed step (512 MiB write); each step timed with CUDA events",
                        "wall_ms_per_step": wall * 1e3 / args.steps},
             "roofline": roof, "cpu_baseline": base, "e2e": e2e, "variants": variants,

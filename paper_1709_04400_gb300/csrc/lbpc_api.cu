@@ -357,8 +357,10 @@ LBPC_API lbpc_status lbpc_create(const lbpc_params* p, void* ws, size_t bytes, v
   c->step = 0;
   c->err = LBPC_OK;
   c->msg[0] = 0;
+  c->buf.fused_tile = lbpc::kDefaultFusedTile;
   for (int k = 0; k < 2; ++k)
-    if (lbpc::fused_tma_encode(&c->tma[k], p->prec, 0, c->buf.f[k], c->buf.g[k], c->buf.ref_f[k], c->buf.ref_g[k], c->dp))
+    if (lbpc::fused_tma_encode(&c->tma[k], p->prec, c->buf.fused_tile, c->buf.f[k], c->buf.g[k], c->buf.ref_f[k],
+                               c->buf.ref_g[k], c->dp))
       c->buf.tma[k] = &c->tma[k];
   *out = c;
   return LBPC_OK;
