@@ -186,6 +186,17 @@ def _dtypes():
     return {lbpc.FP64: "f64", lbpc.DF64: "df64 (f32 pair)", lbpc.FP32: "f32", lbpc.FP16DEV: "f32 (f16 storage)"}
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels this bench
+# reports, from one-pass ncu captures of the same commands (profiles/dram_traffic.md), keyed by
+# (kernel, workload, storage). They describe the kernels as built when they were taken; a change to a
+# kernel must refresh its entry or remove it (the line then reports null).
+MEASURED_TRAFFIC = {
+    ("k_collide", "droplet_evaporation_256_dT0.1Tc", "fp64"): 14_740_352,
+    ("k_fused", "droplet_evaporation_4096_dT0.1Tc", "fp32"): 2_507_959_552,
+    ("k_collide", "droplet_evaporation_2048_dT0.1Tc", "df64"): 1_639_175_680,
+}
+
+
 def _peak_hbm():
     """Measured copy bandwidth of the GB300s in GB/s (fallback 6800)."""
     try:
@@ -275,20 +286,22 @@ def run_native(args):
         flops = fpn * N
         achieved = flops / (avg["k_collide"] / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": "k_collide", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
-                "frac": achieved / 1.25, "traffic": None,
+                "frac": achieved / 1.25, "traffic": MEASURED_TRAFFIC.get(("k_collide", case["name"], prec_name)),
                 "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s, profiling recipe); 1.20 measured FMA",
                 "flops_per_node": fpn, "top_kernel": top}
     elif "k_fused" in avg:
         bytes_ = fused_bytes_per_node(pb) * N
         achieved = bytes_ / (avg["k_fused"] / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": "k_fused", "achieved": achieved, "peak": peak_bw, "unit": "GB/s",
-                "frac": achieved / peak_bw, "traffic": None, "peak_source": bw_src,
+                "frac": achieved / peak_bw, "traffic": MEASURED_TRAFFIC.get(("k_fused", case["name"], prec_name)),
+                "peak_source": bw_src,
                 "bytes_per_node": fused_bytes_per_node(pb), "top_kernel": top}
     else:
         bytes_ = collide_bytes_per_node(pb) * N
         achieved = bytes_ / (avg["k_collide"] / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak_bw, "unit": "GB/s",
-                "frac": achieved / peak_bw, "traffic": None, "peak_source": bw_src,
+                "frac": achieved / peak_bw, "traffic": MEASURED_TRAFFIC.get(("k_collide", case["name"], prec_name)),
+                "peak_source": bw_src,
                 "bytes_per_node": collide_bytes_per_node(pb), "top_kernel": top}
 
     # the same workload in double-word arithmetic (LBPC_DF64: pairs of binary32 on the FP32 pipes, held
