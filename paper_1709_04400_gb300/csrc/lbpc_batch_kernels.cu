@@ -64,44 +64,55 @@ __global__ void __launch_bounds__(TX* TY / NPT, fused_min_blocks<S, TX * TY / NP
   __shared__ FusedSmem<R, TX, TY> sm;
   __shared__ BatchInst<S> sI[2];
   __shared__ BatchTile st[3];  // this tile's entry, the next one's, and the one after (filled while computing)
-  const int ntiles = meta->ntiles;
-  const BatchTile* __restrict__ tiles = meta->tiles;
+  // walk state (work-list position, descriptor slot, ring position), kept in shared memory so that no
+  // register holds it across the tile body
+  __shared__ int s_t, s_slot, s_r;
   const int G = gridDim.x;
-  int t = blockIdx.x;
-  if (t >= ntiles) return;
+  if ((int)blockIdx.x >= meta->ntiles) return;
   if (threadIdx.x == 0) {
-    st[0] = tiles[t];
-    if (t + G < ntiles) st[1] = tiles[t + G];
+    const int t0 = blockIdx.x, n = meta->ntiles;
+    st[0] = meta->tiles[t0];
+    if (t0 + G < n) st[1] = meta->tiles[t0 + G];
+    s_t = t0;
+    s_slot = 0;
+    s_r = 0;
   }
   __syncthreads();
   desc_copy_async<S, R>(&sI[0], &insts[st[0].inst]);
   cp_async_wait_all();
   __syncthreads();
-  int slot = 0, r = 0;  // descriptor slot of this tile; ring position of this tile's entry
   for (;;) {
-    const BatchTile tile = st[r];
-    const int rn = r == 2 ? 0 : r + 1, ra = rn == 2 ? 0 : rn + 1;
-    const bool more = t + G < ntiles;
-    const bool change = more && st[rn].inst != tile.inst;
-    if (change) desc_copy_async<S, R>(&sI[slot ^ 1], &insts[st[rn].inst]);
-    if (threadIdx.x == NTH - 1 && t + 2 * G < ntiles) cp_async16(&st[ra], &tiles[t + 2 * G]);
-    const BatchInst<S>& I = sI[slot];
-    const DevParams& P = I.P;
-    const int cur = I.cur;
-    const long long step = I.step;
-    const bool interior = tile.x0 >= 3 && tile.x0 + TX + 3 <= P.nx && tile.y0 >= 3 && tile.y0 + TY + 3 <= P.ny;
-    if (interior)
-      fused_body<1, S, R, TX, TY, NPT>(I.f[cur], I.g[cur], I.f[cur ^ 1], I.g[cur ^ 1], (R*)I.phi_prev, P, step,
-                                       step == 0, I.scalars, I.partials, I.status, sm, tile.x0, tile.y0, tile.pslot);
-    else
-      fused_body<0, S, R, TX, TY, NPT>(I.f[cur], I.g[cur], I.f[cur ^ 1], I.g[cur ^ 1], (R*)I.phi_prev, P, step,
-                                       step == 0, I.scalars, I.partials, I.status, sm, tile.x0, tile.y0, tile.pslot);
+    {
+      const int t = s_t, slot = s_slot, r = s_r, ntiles = meta->ntiles;
+      const BatchTile tile = st[r];
+      const int rn = r == 2 ? 0 : r + 1, ra = rn == 2 ? 0 : rn + 1;
+      const bool more = t + G < ntiles;
+      if (more && st[rn].inst != tile.inst) desc_copy_async<S, R>(&sI[slot ^ 1], &insts[st[rn].inst]);
+      if (threadIdx.x == NTH - 1 && t + 2 * G < ntiles) cp_async16(&st[ra], &meta->tiles[t + 2 * G]);
+      const BatchInst<S>& I = sI[slot];
+      const DevParams& P = I.P;
+      const int cur = I.cur;
+      const long long step = I.step;
+      const bool interior = tile.x0 >= 3 && tile.x0 + TX + 3 <= P.nx && tile.y0 >= 3 && tile.y0 + TY + 3 <= P.ny;
+      if (interior)
+        fused_body<1, S, R, TX, TY, NPT>(I.f[cur], I.g[cur], I.f[cur ^ 1], I.g[cur ^ 1], (R*)I.phi_prev, P, step,
+                                         step == 0, I.scalars, I.partials, I.status, sm, tile.x0, tile.y0, tile.pslot);
+      else
+        fused_body<0, S, R, TX, TY, NPT>(I.f[cur], I.g[cur], I.f[cur ^ 1], I.g[cur ^ 1], (R*)I.phi_prev, P, step,
+                                         step == 0, I.scalars, I.partials, I.status, sm, tile.x0, tile.y0, tile.pslot);
+    }
     cp_async_wait_all();
     __syncthreads();  // the tile is done with the shared memory; the next descriptor and entry have landed
-    if (!more) break;
-    if (change) slot ^= 1;
-    t += G;
-    r = rn;
+    const int t = s_t, r = s_r, rn = r == 2 ? 0 : r + 1;
+    if (t + G >= meta->ntiles) break;
+    const bool change = st[rn].inst != st[r].inst;
+    __syncthreads();  // every thread has read the walk state
+    if (threadIdx.x == 0) {
+      s_t = t + G;
+      s_r = rn;
+      if (change) s_slot ^= 1;
+    }
+    __syncthreads();
   }
 }
 
