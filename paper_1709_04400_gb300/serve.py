@@ -156,25 +156,19 @@ class Server:
                 continue
             chunk = min(self.max_chunk, min(v[1] for v in self.active.values()))
             self.batch.step(chunk)
-            failed = set()
-            try:
-                self.batch.check()
-            except lbpc.LbpcError as e:
-                failed.add(getattr(e, "instance", -1))
-                while True:  # every other failed instance as well
-                    for i in failed:
-                        if i in self.active:
-                            self.active[i][1] = 0
-                    try:
-                        self._retire(self.clock() - self.t0, failed_ids=failed)
-                        self.batch.check()
-                        break
-                    except lbpc.LbpcError as e2:
-                        failed = {getattr(e2, "instance", -1)}
-            for v in self.active.values():
+            for v in self.active.values():  # every active instance took the chunk's steps
                 v[1] -= chunk
                 self.node_steps += chunk * v[3]
             self.chunks += 1
+            while True:  # retire failed instances one by one until the check passes
+                try:
+                    self.batch.check()
+                    break
+                except lbpc.LbpcError as e:
+                    i = getattr(e, "instance", None)
+                    if e.status != lbpc.LBPC_ENONPHYS or i not in self.active:
+                        raise  # not a per-instance failure: nothing to retire
+                    self._retire(self.clock() - self.t0, failed_ids={i})
             self._retire(self.clock() - self.t0)
         self.makespan = self.clock() - self.t0
         return self.results

@@ -157,3 +157,31 @@ def test_arena_full_and_slot_reuse():
     b.step(3)
     assert b.step_count(i3) == 3 and b.step_count(i2) == 3
     b.close()
+
+
+def test_failed_instance_named_and_others_unaffected():
+    """One instance starts with a density beyond the EOS pole (1/b = 10.5). The check names that instance
+    and the first bad node. Once it is removed, the check passes again, and the other instances
+    equal, bit for bit, their runs in batches of their own."""
+    prec = lbpc.FP32
+    cases = _cases()[:3]
+    bad_case, bad_rho, bad_T = workloads.droplet_periodic(TC, RV, RL, n=32, radius=8.0)
+    bad_rho = bad_rho.copy()
+    bad_rho[7, 11] = 11.0
+    b = lbpc.Batch(prec, _arena_for(cases + [(bad_case, bad_rho, bad_T)], prec))
+    ids = [b.add(lbpc.params_from_case(c, prec), r, t) for c, r, t in cases[:2]]
+    ib = b.add(lbpc.params_from_case(bad_case, prec), bad_rho, bad_T)
+    ids.append(b.add(lbpc.params_from_case(cases[2][0], prec), cases[2][1], cases[2][2]))
+    b.step(5)
+    with pytest.raises(lbpc.LbpcError) as e:
+        b.check()
+    assert e.value.status == lbpc.LBPC_ENONPHYS and e.value.instance == ib
+    assert f"instance {ib}: non-physical state at step 0, node (x=11, y=7)" in str(e.value)
+    b.remove(ib)
+    b.check()
+    b.step(7)
+    for i, (c, r, t) in zip(ids, cases):
+        assert b.step_count(i) == 12
+        for a, ex in zip(b.fields(i), _solo(c, r, t, 12, prec)):
+            assert np.array_equal(a, ex), c["name"]
+    b.close()

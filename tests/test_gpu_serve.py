@@ -68,3 +68,34 @@ def _eos():
     Tc, _ = lbpc.eos_critical(p0)
     rv, rl, _ = lbpc.coexistence(p0, 0.86 * Tc)
     return Tc, rv, rl
+
+
+def test_failed_request_retired_while_others_complete(monkeypatch):
+    """A request whose initial state holds a density beyond the EOS pole fails after the first chunk
+    with the steps it ran; the requests around it complete and equal their runs alone."""
+    reqs = _stream()[:4]
+    bad = reqs[1].rid
+    real = serve.make_case
+
+    def planted(req, *a):
+        case, rho, T = real(req, *a)
+        if req.rid == bad:
+            rho = rho.copy()
+            rho[3, 5] = 11.0
+        return case, rho, T
+
+    monkeypatch.setattr(serve, "make_case", planted)
+    srv = serve.Server(prec=lbpc.FP32, hbm_budget_bytes=256 << 20, max_chunk=16, keep_fields=True)
+    results = {r.rid: r for r in srv.run([serve.Request(**{**r.__dict__, "arrival": 0.0}) for r in reqs])}
+    st = srv.stats()
+    srv.close()
+    assert results[bad].status == "failed" and results[bad].message == "non-physical state"
+    assert 0 < results[bad].steps <= 16
+    assert st["failed"] == 1 and st["ok"] == len(reqs) - 1
+    monkeypatch.setattr(serve, "make_case", real)
+    for req in reqs:
+        if req.rid != bad:
+            res = results[req.rid]
+            assert res.status == "ok" and res.steps == req.steps
+            for a, e in zip(res.fields, _alone(req)):
+                assert np.array_equal(a, e), req.rid
