@@ -62,8 +62,12 @@ typedef enum { LBPC_FP64 = 0, LBPC_FP32 = 1, LBPC_FP16DEV = 2, LBPC_DF64 = 3 } l
 
 /* Flow boundary of an edge. x edges must be periodic; y edges are both periodic or both not.
  * A non-periodic y edge is an on-node row closed by the Zou-He scheme (the paper applies Zou-He at
- * the solid surface, Sec. IV A, citing its Ref. [51]): LBPC_WALL = no-slip wall (u = 0),
- * LBPC_PRESSURE = fixed density rho_bc with u_x = 0 (the open / fixed-pressure top). */
+ * the solid surface, Sec. IV A, citing its Ref. [51]): LBPC_WALL = no-slip wall, LBPC_PRESSURE =
+ * fixed density rho_bc with u_x = 0 (the open / fixed-pressure top). A wall sets the momentum of its
+ * row to j = -F/2, F being the row's force of the previous step, so that the forcing scheme's
+ * velocity v = (j + F/2)/rho vanishes there; with j = 0 a force on the wall row (the adsorption
+ * force, buoyancy) would move fluid through the wall. The state therefore holds the wall rows' force
+ * beside the populations. */
 typedef enum { LBPC_PERIODIC = 0, LBPC_WALL = 1, LBPC_PRESSURE = 2 } lbpc_flow_bc;
 
 /* Thermal boundary of an edge: LBPC_T_DIRICHLET holds T = T_bc on the edge row/column (the
@@ -104,7 +108,8 @@ typedef struct {
   double rho_bc[4];        /* density held on LBPC_PRESSURE edges */
   double T_bc[4];          /* temperature held on LBPC_T_DIRICHLET edges */
   double T_strip;          /* temperature of the heated strip */
-  double G_wall;           /* fluid-solid strength: F_ads = -G_wall psi(x) sum_a w_a s(x+e_a) e_a at walls */
+  double G_wall;           /* fluid-solid strength: F_ads = -G_wall psi(x) sum_a w_a s(x+e_a) e_a at the
+                              y- wall (G_wall < 0 wets); a y+ wall is a neutral lid */
 } lbpc_params;
 
 /* Library version (LBPC_VERSION). */
@@ -187,7 +192,8 @@ lbpc_status lbpc_sums(lbpc_ctx* c, double* mass, double* heat);
  *   - a 512-byte header: magic, version, the lbpc_params, the step counter and the lagged rho_ave;
  *   - the current post-collision populations f and g in the storage type, plus the FP16 reference
  *     planes for LBPC_FP16DEV;
- *   - phi of the previous step, in the arithmetic type.
+ *   - phi of the previous step, in the arithmetic type;
+ *   - the wall rows' force of the previous step (binary64 [4][nx]), which the next wall closure uses.
  * Stepping a context restored from a checkpoint taken after k steps reproduces, bit for bit, the
  * steps after k of an uninterrupted run with the same parameters and precision.
  *
@@ -307,6 +313,11 @@ void lbpc_batch_destroy(lbpc_batch* b);
  *             that node x + e_a receives when it streams. A context's state has this form.
  *   f_out,g_out  device buffers of the same size for the new post-collision populations; they must
  *             not alias the inputs
+ *   wall_in   device [4][nx] doubles: the force on the wall rows (y- Fx, y- Fy, y+ Fx, y+ Fy) of the
+ *             step that wrote f_in, zeros before the first step; entries of a non-wall edge are unused.
+ *             Required when a y edge is LBPC_WALL, else it may be NULL
+ *   wall_out  device [4][nx] doubles for this step's wall-row force (the next call's wall_in); it
+ *             must not alias wall_in. Required and ignored as wall_in
  *   phi_prev  device [ny][nx] of the arithmetic type: phi of the previous step in, this step's out
  *             (ignored on input when step == 0)
  *   rho_ave   device pointer to one double: the previous step's domain mean of rho in, this step's
@@ -323,7 +334,8 @@ void lbpc_batch_destroy(lbpc_batch* b);
  * GPU, from several threads or streams, race on it. */
 #define LBPC_STATIC_MAX_NODES (256 * 256)
 lbpc_status lbpc_step_static(const lbpc_params* p, const void* f_in, const void* g_in, void* f_out, void* g_out,
-                             void* phi_prev, double* rho_ave, int64_t step, void* stream);
+                             const double* wall_in, double* wall_out, void* phi_prev, double* rho_ave, int64_t step,
+                             void* stream);
 
 #ifdef __cplusplus
 }

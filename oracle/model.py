@@ -23,17 +23,20 @@ READINGS (the paper is silent or delegates; every one is also listed in the desi
     m* = m - Lambda (m - m_eq) + (I - Lambda/2) S_F with the sigma term in the energy moments.
   * Isotropic differences: d_i X = 3 sum_a w_a X(x+e_a) e_ai, lap X = 6 sum_a w_a (X(x+e_a) - X(x)).
   * First step: phi(t - dt) := phi(t). rho_ave lags one step (step 0 uses the initial mean).
-  * x is periodic. A non-periodic y edge is an on-node row: a no-slip wall (Zou-He, u = 0) or a
+  * x is periodic. A non-periodic y edge is an on-node row: a no-slip wall (Zou-He, v = 0 for the
+    forcing scheme's velocity, so j = -F/2 with the wall row's force of the step before) or a
     fixed-density edge (Zou-He, u_x = 0). Stencils that cross such an edge, F_int's included, see
-    ghost rows that copy the edge row (zero gradient), so a wall with G_w = 0 is neutral; at a wall
-    the adsorption force F_ads = -G_w psi(x) sum_a w_a s(x + e_a) e_a (s = 1 on the solid ghost row)
-    sets the wettability (G_w < 0 attracts liquid).
+    ghost rows that copy the edge row (zero gradient), so a wall with G_w = 0 is neutral; at the y-
+    wall the adsorption force F_ads = -G_w psi(x) sum_a w_a s(x + e_a) e_a (s = 1 on the solid ghost
+    row) sets the wettability (G_w < 0 attracts liquid). A y+ wall is a neutral lid: every solid
+    surface of Sec. IV (the droplet on a surface, the heated wall) is the bottom one.
   * A held temperature on a non-periodic y edge (wall rows, the heated strip) enters through the
     unknown g by anti-bounce-back; without one those g bounce back (zero heat flux). A Dirichlet
     ring inside a periodic domain resets its nodes to g := M^{-1} m_eq(T_bc, v = 0).
 
 Test hooks (never used by the GPU path): ``frozen_flow=(vx, vy)`` keeps f fixed and imposes a
-uniform v with F = 0; ``frozen_thermal=True`` keeps g fixed.
+uniform v with F = 0; ``frozen_thermal=True`` keeps g fixed; ``body_force=(ax, ay)`` adds the force
+rho * (ax, ay), which drives a fluid of uniform density (plane Poiseuille flow).
 """
 
 from dataclasses import dataclass, field
@@ -82,6 +85,7 @@ class OracleParams:
     G_wall: float = 0.0
     model: str = "improved"  # improved | compromised | gong_cheng
     frozen_flow: Optional[Tuple[float, float]] = None
+    body_force: Optional[Tuple[float, float]] = None
     frozen_thermal: bool = False
 
     def check(self):
@@ -217,14 +221,10 @@ def macroscopic(p: OracleParams, s: OracleState):
         Fx = Fy = Fix = Fiy = np.zeros_like(rho)
     else:
         # 3. force: pseudopotential interaction, adsorption at walls, buoyancy (Sec. IV B)
-        wall_lo = p.flow_bc[2] == "wall"
-        wall_hi = p.flow_bc[3] == "wall"
         pse = _extend(psi, p, ghost="copy")
         solid = np.zeros_like(pse)
-        if wall_lo:
+        if p.flow_bc[2] == "wall":  # the wettable surface is the y- wall only (a y+ wall is neutral)
             solid[0, :] = 1.0
-        if wall_hi:
-            solid[-1, :] = 1.0
         wF = {1: 1.0 / 3.0, 2: 1.0 / 12.0}
         sx = sum(wF[L.EX[a] ** 2 + L.EY[a] ** 2] * _nb(pse, a) * L.EX[a] for a in range(1, 9))
         sy = sum(wF[L.EX[a] ** 2 + L.EY[a] ** 2] * _nb(pse, a) * L.EY[a] for a in range(1, 9))
@@ -236,6 +236,9 @@ def macroscopic(p: OracleParams, s: OracleState):
         if p.buoyancy:
             Fx = Fx + (rho - s.rho_ave) * p.gx
             Fy = Fy + (rho - s.rho_ave) * p.gy
+        if p.body_force is not None:
+            Fx = Fx + rho * p.body_force[0]
+            Fy = Fy + rho * p.body_force[1]
         # 4. velocity including half the force
         vx = (jx + 0.5 * Fx) / rho
         vy = (jy + 0.5 * Fy) / rho
@@ -318,18 +321,29 @@ def stream(pop):
     return out
 
 
-def flow_boundaries(p: OracleParams, f):
+def flow_boundaries(p: OracleParams, f, F=None):
     """Zou-He closures on non-periodic y edges (READING of Ref. [51]; u = 0 at a wall, u_x = 0 and
-    rho = rho_bc at a pressure edge). Unknowns at y- are f2, f5, f6; at y+ they are f4, f7, f8."""
+    rho = rho_bc at a pressure edge). Unknowns at y- are f2, f5, f6; at y+ they are f4, f7, f8.
+
+    At a wall the closure sets the momentum j = sum e f to -F/2, so that the velocity of the forcing
+    scheme, v = (j + F/2)/rho, vanishes there (READING: with j = 0 a force on the wall row, such as
+    the adsorption force, moves the fluid through the wall at F/(2 rho) and the wall drains mass).
+    F = (Fx, Fy) is the force of the step that produced f, one step behind the step that will use
+    the closed state; None (the initial state) means F = 0."""
     for edge, row in (("y-", 0), ("y+", -1)):
         kind = p.flow_bc[EDGES.index(edge)]
         if kind == "periodic":
             continue
         q = [f[a, row].copy() for a in range(9)]
         d13 = q[1] - q[3]
+        if kind == "wall":
+            jx = np.zeros_like(q[0]) if F is None else -0.5 * F[0][row]
+            jy = np.zeros_like(q[0]) if F is None else -0.5 * F[1][row]
         if edge == "y-":
-            if kind == "wall":
-                f[2, row], f[5, row], f[6, row] = q[4], q[7] - 0.5 * d13, q[8] + 0.5 * d13
+            if kind == "wall":  # Zou-He for a prescribed j: f2 - f4 = 2/3 j_y, and j_x from f5 - f6
+                f[2, row] = q[4] + 2.0 / 3.0 * jy
+                f[5, row] = q[7] - 0.5 * d13 + 0.5 * jx + jy / 6.0
+                f[6, row] = q[8] + 0.5 * d13 - 0.5 * jx + jy / 6.0
             else:
                 rb = p.rho_bc[2]
                 ru = rb - (q[0] + q[1] + q[3] + 2.0 * (q[4] + q[7] + q[8]))  # rho_bc * u_y
@@ -338,7 +352,9 @@ def flow_boundaries(p: OracleParams, f):
                 f[6, row] = q[8] + 0.5 * d13 + ru / 6.0
         else:
             if kind == "wall":
-                f[4, row], f[7, row], f[8, row] = q[2], q[5] + 0.5 * d13, q[6] - 0.5 * d13
+                f[4, row] = q[2] - 2.0 / 3.0 * jy
+                f[7, row] = q[5] + 0.5 * d13 - 0.5 * jx - jy / 6.0
+                f[8, row] = q[6] - 0.5 * d13 + 0.5 * jx - jy / 6.0
             else:
                 rb = p.rho_bc[3]
                 ru = (q[0] + q[1] + q[3] + 2.0 * (q[2] + q[5] + q[6])) - rb  # rho_bc * u_y
@@ -400,7 +416,10 @@ def step(p: OracleParams, s: OracleState) -> OracleState:
         S0 = phi + 0.5 * (phi - phi_prev)  # Eq. 46 with d_t phi ~ [phi(t) - phi(t - dt)] / dt
     else:
         S0 = phi
-    fn = s.f if p.frozen_flow is not None else flow_boundaries(p, stream(collide_flow(p, s.f, mac)))
+    if p.frozen_flow is not None:
+        fn = s.f
+    else:
+        fn = flow_boundaries(p, stream(collide_flow(p, s.f, mac)), (mac["Fx"], mac["Fy"]))
     gn = s.g if p.frozen_thermal else heat_boundaries(p, stream(collide_heat(p, s.g, mac, S0)))
     return OracleState(f=fn, g=gn, phi_prev=phi, rho_ave=float(np.mean(mac["rho"])), step=s.step + 1, last=mac)
 

@@ -59,7 +59,7 @@ void set_msg(char* dst, size_t n, const char* fmt, ...) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t f[2], g[2], ref_f[2], ref_g[2], phi, planes, partials, scalars, status, total;
+  size_t f[2], g[2], ref_f[2], ref_g[2], wall[2], phi, planes, partials, scalars, status, total;
   size_t store, real;
   long long N;
   int nblocks;
@@ -82,6 +82,9 @@ Layout layout_of(const lbpc_params* p) {
   for (int k = 0; k < 2; ++k) {
     L.ref_f[k] = off; off += ref;
     L.ref_g[k] = off; off += ref;
+  }
+  for (int k = 0; k < 2; ++k) {  // wall-row forces kept with f (A/B) for the next step's wall closure
+    L.wall[k] = off; off += align256((size_t)lbpc::wall_doubles(p->nx) * sizeof(double));
   }
   L.phi = off; off += align256((size_t)L.N * L.real);
   L.planes = off; off += (size_t)lbpc::split_nplanes() * align256((size_t)L.N * L.real);
@@ -345,6 +348,7 @@ LBPC_API lbpc_status lbpc_create(const lbpc_params* p, void* ws, size_t bytes, v
     c->buf.g[k] = base + L.g[k];
     c->buf.ref_f[k] = p->prec == LBPC_FP16DEV ? (float*)(base + L.ref_f[k]) : nullptr;
     c->buf.ref_g[k] = p->prec == LBPC_FP16DEV ? (float*)(base + L.ref_g[k]) : nullptr;
+    c->buf.wall[k] = (double*)(base + L.wall[k]);
   }
   c->stage_bytes = 2 * (L.g[0] - L.f[0]);
   c->buf.phi_prev = base + L.phi;
@@ -537,9 +541,11 @@ LBPC_API lbpc_status lbpc_fields(lbpc_ctx* c, double* rho, double* ux, double* u
 
 // ---- checkpoint / resume ----
 // Layout: a 512-byte header, then f and g of the current state (storage type, [9][N] each), the FP16
-// reference planes of f and g (FP16 storage only), and phi_prev ([N] of the arithmetic type).
+// reference planes of f and g (FP16 storage only), phi_prev ([N] of the arithmetic type) and the wall
+// rows' force kept with f (FP64 [4][nx]).
 namespace {
 constexpr char kCkptMagic[8] = {'L', 'B', 'P', 'C', 'C', 'K', 'P', '1'};
+constexpr uint32_t kCkptVersion = 2;  // 2: the wall-force section
 constexpr size_t kCkptHeader = 512;
 struct CkptHeader {
   char magic[8];
@@ -547,24 +553,25 @@ struct CkptHeader {
   lbpc_params params;  // no padding inside the struct: compared bytewise on load
   int64_t step;
   double rho_ave;
-  uint64_t pop_bytes, ref_bytes, phi_bytes;
+  uint64_t pop_bytes, ref_bytes, phi_bytes, wall_bytes;
 };
 static_assert(sizeof(CkptHeader) <= kCkptHeader, "checkpoint header fits its slot");
 static_assert(sizeof(lbpc_params) == 16 * 4 + 39 * 8, "lbpc_params has no padding");
 
-void ckpt_sizes(const lbpc_ctx* c, size_t& pop, size_t& ref, size_t& phi) {
+void ckpt_sizes(const lbpc_ctx* c, size_t& pop, size_t& ref, size_t& phi, size_t& wall) {
   const Layout L = layout_of(&c->p);
   pop = 9 * (size_t)L.N * L.store;
   ref = c->p.prec == LBPC_FP16DEV ? (size_t)L.N * sizeof(float) : 0;
   phi = (size_t)L.N * L.real;
+  wall = (size_t)lbpc::wall_doubles(c->p.nx) * sizeof(double);
 }
 }  // namespace
 
 LBPC_API size_t lbpc_checkpoint_bytes(const lbpc_ctx* c) {
   if (!c) return 0;
-  size_t pop, ref, phi;
-  ckpt_sizes(c, pop, ref, phi);
-  return kCkptHeader + 2 * pop + 2 * ref + phi;
+  size_t pop, ref, phi, wall;
+  ckpt_sizes(c, pop, ref, phi, wall);
+  return kCkptHeader + 2 * pop + 2 * ref + phi + wall;
 }
 
 LBPC_API lbpc_status lbpc_save(lbpc_ctx* c, void* buf, size_t bytes, int on_device) {
@@ -574,17 +581,18 @@ LBPC_API lbpc_status lbpc_save(lbpc_ctx* c, void* buf, size_t bytes, int on_devi
   if (!c->initialised) return fail(c, LBPC_ESTATE, "lbpc_save before lbpc_init");
   if (bytes < lbpc_checkpoint_bytes(c)) return LBPC_EINVAL;
   DeviceGuard g(c->device);
-  size_t pop, ref, phi;
-  ckpt_sizes(c, pop, ref, phi);
+  size_t pop, ref, phi, wall;
+  ckpt_sizes(c, pop, ref, phi, wall);
   CkptHeader h{};
   memcpy(h.magic, kCkptMagic, sizeof h.magic);
-  h.version = 1;
+  h.version = kCkptVersion;
   h.header_bytes = (uint32_t)kCkptHeader;
   h.params = c->p;
   h.step = c->step;
   h.pop_bytes = pop;
   h.ref_bytes = ref;
   h.phi_bytes = phi;
+  h.wall_bytes = wall;
   CU(c, cudaMemcpyAsync(&h.rho_ave, c->buf.scalars, sizeof(double), cudaMemcpyDeviceToHost, c->stream),
      "lbpc_save rho_ave");
   CU(c, cudaStreamSynchronize(c->stream), "lbpc_save sync");
@@ -607,6 +615,8 @@ LBPC_API lbpc_status lbpc_save(lbpc_ctx* c, void* buf, size_t bytes, int on_devi
     off += ref;
   }
   CU(c, cudaMemcpyAsync(dst + off, c->buf.phi_prev, phi, d2x, c->stream), "lbpc_save phi_prev");
+  off += phi;
+  CU(c, cudaMemcpyAsync(dst + off, c->buf.wall[c->cur], wall, d2x, c->stream), "lbpc_save wall");
   CU(c, cudaStreamSynchronize(c->stream), "lbpc_save sync");
   return LBPC_OK;
 }
@@ -624,13 +634,13 @@ LBPC_API lbpc_status lbpc_load(lbpc_ctx* c, const void* buf, size_t bytes, int o
   } else {
     memcpy(&h, src, sizeof h);
   }
-  size_t pop, ref, phi;
-  ckpt_sizes(c, pop, ref, phi);
-  if (memcmp(h.magic, kCkptMagic, sizeof h.magic) != 0 || h.version != 1 || h.header_bytes != kCkptHeader)
+  size_t pop, ref, phi, wall;
+  ckpt_sizes(c, pop, ref, phi, wall);
+  if (memcmp(h.magic, kCkptMagic, sizeof h.magic) != 0 || h.version != kCkptVersion || h.header_bytes != kCkptHeader)
     return fail(c, LBPC_EINVAL, "lbpc_load: not a liblbpc checkpoint");
   if (memcmp(&h.params, &c->p, sizeof(lbpc_params)) != 0)
     return fail(c, LBPC_EINVAL, "lbpc_load: the checkpoint was taken with other parameters");
-  if (h.pop_bytes != pop || h.ref_bytes != ref || h.phi_bytes != phi || h.step < 0)
+  if (h.pop_bytes != pop || h.ref_bytes != ref || h.phi_bytes != phi || h.wall_bytes != wall || h.step < 0)
     return fail(c, LBPC_EINVAL, "lbpc_load: section sizes do not match");
   const cudaMemcpyKind x2d = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   size_t off = kCkptHeader;
@@ -645,6 +655,8 @@ LBPC_API lbpc_status lbpc_load(lbpc_ctx* c, const void* buf, size_t bytes, int o
     off += ref;
   }
   CU(c, cudaMemcpyAsync(c->buf.phi_prev, src + off, phi, x2d, c->stream), "lbpc_load phi_prev");
+  off += phi;
+  CU(c, cudaMemcpyAsync(c->buf.wall[0], src + off, wall, x2d, c->stream), "lbpc_load wall");
   CU(c, cudaMemcpyAsync(c->buf.scalars, &h.rho_ave, sizeof(double), cudaMemcpyHostToDevice, c->stream),
      "lbpc_load rho_ave");
   CU(c, cudaMemsetAsync(c->buf.status, 0, 8 * sizeof(long long), c->stream), "lbpc_load status reset");

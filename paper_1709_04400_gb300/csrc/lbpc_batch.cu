@@ -85,7 +85,7 @@ struct HostInst {
   lbpc::DevParams dp{};
   long long N = 0;
   size_t off = 0, bytes = 0;  // arena block of the instance
-  size_t f[2], g[2], rf[2], rg[2], phi, partials, scalars;
+  size_t f[2], g[2], rf[2], rg[2], wall[2], phi, partials, scalars;
   size_t npartials = 0;
   long long step = 0;
   int cur = 0;
@@ -112,6 +112,9 @@ size_t layout_instance(const lbpc_params* p, HostInst* h) {
   for (int k = 0; k < 2; ++k) {
     h->rf[k] = off; off += ref;
     h->rg[k] = off; off += ref;
+  }
+  for (int k = 0; k < 2; ++k) {  // wall-row forces kept with f for the next step's wall closure
+    h->wall[k] = off; off += a256((size_t)lbpc::wall_doubles(p->nx) * sizeof(double));
   }
   h->phi = off; off += a256((size_t)N * rb);
   h->npartials = std::max(max_tiles(p), 2 * (size_t)((N + lbpc::split_block() - 1) / lbpc::split_block()));
@@ -187,7 +190,8 @@ template <class S> void fill_desc(lbpc_batch* b, int k, std::vector<char>& out) 
     char* base = b->base + h.off;
     d.P = h.dp;
     for (int j = 0; j < 2; ++j) {
-      d.f[j] = lbpc::PopBuf<S>{(S*)(base + h.f[j]), b->prec == LBPC_FP16DEV ? (float*)(base + h.rf[j]) : nullptr};
+      d.f[j] = lbpc::PopBuf<S>{(S*)(base + h.f[j]), b->prec == LBPC_FP16DEV ? (float*)(base + h.rf[j]) : nullptr,
+                               (double*)(base + h.wall[j])};
       d.g[j] = lbpc::PopBuf<S>{(S*)(base + h.g[j]), b->prec == LBPC_FP16DEV ? (float*)(base + h.rg[j]) : nullptr};
     }
     d.phi_prev = base + h.phi;
@@ -267,6 +271,7 @@ lbpc::SplitBuffers split_view(lbpc_batch* b, const HostInst& h, char* scratch) {
     s.g[j] = base + h.g[j];
     s.ref_f[j] = b->prec == LBPC_FP16DEV ? (float*)(base + h.rf[j]) : nullptr;
     s.ref_g[j] = b->prec == LBPC_FP16DEV ? (float*)(base + h.rg[j]) : nullptr;
+    s.wall[j] = (double*)(base + h.wall[j]);
   }
   s.phi_prev = base + h.phi;
   s.partials = (double*)(base + h.partials);

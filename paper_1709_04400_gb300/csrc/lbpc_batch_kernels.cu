@@ -41,6 +41,7 @@ __device__ __forceinline__ void desc_copy_async(BatchInst<S>* dst, const BatchIn
                     sizeof(BatchInst<S>) % 16 == 0,
                 "descriptor parts must be 16-byte aligned");
   static_assert(CoefSpan<R>::off + 16 * COEF <= sizeof(DevParams), "coefficient span inside the parameters");
+  static_assert(HEAD + COEF + TAIL <= 128, "one copy per thread of the (at least 128) threads");
   const unsigned char* s = (const unsigned char*)src;
   unsigned char* d = (unsigned char*)dst;
   const int k = threadIdx.x;

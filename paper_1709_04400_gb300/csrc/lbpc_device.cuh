@@ -144,10 +144,21 @@ template <class R> __device__ __forceinline__ void eos(R rho, R T, const DevPara
 // w_a * ref of the node that stored it, ref being that node's density (f) or post-collision
 // temperature (g), held in an FP32 plane beside the populations. The collision conserves the zeroth
 // moment, so the deviations are of order |u| w rho and keep binary16's 11 bits relative to them.
+//
+// A flow buffer also carries the force on its wall rows (`wall`, FP64 [edge y-/y+][Fx/Fy][nx]), written
+// by the step that stored the populations: the next step's wall closure sets j = -F/2 from it.
 template <class S> struct PopBuf {
   S* p;
-  float* ref;  // FP16 storage only
+  float* ref;              // FP16 storage only
+  double* wall;  // flow buffers: wall-row forces (null where unused; aggregate init leaves it null)
 };
+
+// Index of a wall row's entries in PopBuf::wall: edge 0 = y-, 1 = y+; component 0 = Fx, 1 = Fy.
+__host__ __device__ __forceinline__ long long wall_slot(int nx, int edge, int comp, int x) {
+  return (long long)(2 * edge + comp) * nx + x;
+}
+// doubles of one wall-force buffer (one parity)
+__host__ __device__ __forceinline__ long long wall_doubles(int nx) { return 4LL * nx; }
 
 template <class S> struct is_half_t { static constexpr bool value = false; };
 template <> struct is_half_t<__half> { static constexpr bool value = true; };
@@ -201,16 +212,22 @@ __device__ __forceinline__ void pull(const PopBuf<S>& src, const R* w, const Dev
   }
 }
 
-// Zou-He closure of the unknown f on a non-periodic y edge (wall: u = 0; pressure: rho = rho_bc, u_x = 0).
-template <class R> __device__ __forceinline__ void flow_closure(R f[9], const DevParams& P, int y) {
+// Zou-He closure of the unknown f on a non-periodic y edge. Wall: the momentum is set to j = -F/2, F
+// being the wall row's force of the step that stored the populations (`wall`, see PopBuf), so that the
+// forcing scheme's velocity v = (j + F/2)/rho vanishes on the wall (a null `wall` reads as F = 0).
+// Pressure: rho = rho_bc, u_x = 0.
+template <class R>
+__device__ __forceinline__ void flow_closure(R f[9], const DevParams& P, int x, int y, const double* wall) {
   if (P.yper) return;
   const Coefs<R>& C = coefs<R>(P);
   const R d13 = f[1] - f[3];
   if (y == 0) {
-    if (P.ybc_lo == BC_WALL) {
-      f[2] = f[4];
-      f[5] = f[7] - d13 * 0.5f;
-      f[6] = f[8] + d13 * 0.5f;
+    if (P.ybc_lo == BC_WALL) {  // f2 - f4 = 2/3 j_y; f5 - f6 closes j_x
+      const R jx = wall ? R(wall[wall_slot(P.nx, 0, 0, x)]) * -0.5f : R(0);
+      const R jy = wall ? R(wall[wall_slot(P.nx, 0, 1, x)]) * -0.5f : R(0);
+      f[2] = f[4] + R(2.0 / 3.0) * jy;
+      f[5] = f[7] - d13 * 0.5f + jx * 0.5f + jy * R(1.0 / 6.0);
+      f[6] = f[8] + d13 * 0.5f - jx * 0.5f + jy * R(1.0 / 6.0);
     } else {
       const R ru = C.rho_bc_lo - (f[0] + f[1] + f[3] + (f[4] + f[7] + f[8]) * 2);  // rho_bc u_y
       f[2] = f[4] + R(2.0 / 3.0) * ru;
@@ -219,9 +236,11 @@ template <class R> __device__ __forceinline__ void flow_closure(R f[9], const De
     }
   } else if (y == P.ny - 1) {
     if (P.ybc_hi == BC_WALL) {
-      f[4] = f[2];
-      f[7] = f[5] + d13 * 0.5f;
-      f[8] = f[6] - d13 * 0.5f;
+      const R jx = wall ? R(wall[wall_slot(P.nx, 1, 0, x)]) * -0.5f : R(0);
+      const R jy = wall ? R(wall[wall_slot(P.nx, 1, 1, x)]) * -0.5f : R(0);
+      f[4] = f[2] - R(2.0 / 3.0) * jy;
+      f[7] = f[5] + d13 * 0.5f - jx * 0.5f - jy * R(1.0 / 6.0);
+      f[8] = f[6] - d13 * 0.5f + jx * 0.5f - jy * R(1.0 / 6.0);
     } else {
       const R ru = (f[0] + f[1] + f[3] + (f[2] + f[5] + f[6]) * 2) - C.rho_bc_hi;  // rho_bc u_y
       f[4] = f[2] - R(2.0 / 3.0) * ru;
@@ -313,8 +332,18 @@ __device__ __forceinline__ void pull_closed(const PopBuf<S>& fsrc, const PopBuf<
   const Coefs<R>& C = coefs<R>(P);
   pull<S, R>(fsrc, C.wf, P, x, y, f);
   pull<S, R>(gsrc, C.wg, P, x, y, g);
-  flow_closure(f, P, y);
+  flow_closure(f, P, x, y, fsrc.wall);
   heat_closure(g, P, x, y);
+}
+
+// Keep the force of a wall-row node for the next step's closure (into the destination flow buffer).
+template <class R>
+__device__ __forceinline__ void wall_force_store(double* wall, const DevParams& P, int x, int y, R Fx, R Fy) {
+  if (P.yper || !wall) return;
+  const int edge = (y == 0 && P.ybc_lo == BC_WALL) ? 0 : (y == P.ny - 1 && P.ybc_hi == BC_WALL) ? 1 : -1;
+  if (edge < 0) return;
+  wall[wall_slot(P.nx, edge, 0, x)] = double(Fx);
+  wall[wall_slot(P.nx, edge, 1, x)] = double(Fy);
 }
 
 // ------------------------------------------------------------------------------------------------

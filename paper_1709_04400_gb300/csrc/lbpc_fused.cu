@@ -71,8 +71,8 @@ template <class S, class R, int TX, int TY, int NPT = 1>
 static cudaError_t fused_impl(const SplitBuffers& b, const DevParams& P, int cur, long long step, cudaStream_t st,
                               cudaEvent_t* ev) {
   dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
-  const PopBuf<S> fs{(S*)b.f[cur], b.ref_f[cur]}, gs{(S*)b.g[cur], b.ref_g[cur]};
-  const PopBuf<S> fd{(S*)b.f[cur ^ 1], b.ref_f[cur ^ 1]}, gd{(S*)b.g[cur ^ 1], b.ref_g[cur ^ 1]};
+  const PopBuf<S> fs{(S*)b.f[cur], b.ref_f[cur], b.wall[cur]}, gs{(S*)b.g[cur], b.ref_g[cur]};
+  const PopBuf<S> fd{(S*)b.f[cur ^ 1], b.ref_f[cur ^ 1], b.wall[cur ^ 1]}, gd{(S*)b.g[cur ^ 1], b.ref_g[cur ^ 1]};
   if (ev) cudaEventRecord(ev[0], st);
   bool staged = false;
   if constexpr (sizeof(S) <= 4) {  // the TMA-staged kernel exists for FP32 and FP16 storage

@@ -46,6 +46,7 @@ struct SplitBuffers {
   void* g[2];        // populations g
   float* ref_f[2];   // FP16 storage: per-node reference density of the stored f deviations (A/B)
   float* ref_g[2];   // FP16 storage: per-node reference temperature of the stored g deviations (A/B)
+  double* wall[2] = {nullptr, nullptr};  // wall-row forces stored with f (A/B, wall_doubles(nx) each); null if y is periodic
   void* phi_prev;    // phi(t - dt), arithmetic type
   void* planes[16];  // scratch planes of the split kernels, arithmetic type
   double* partials;  // 2 * nblocks per-block partial sums

@@ -116,11 +116,9 @@ __global__ void __launch_bounds__(BLOCK) k_force(Planes<R> pl, DevParams P, cons
   const R sy = (c[2][1] - c[0][1]) * R(1.0 / 3.0) + (c[2][2] + c[2][0] - c[0][0] - c[0][2]) * R(1.0 / 12.0);
   const R Fix = -C.G * pc * sx, Fiy = -C.G * pc * sy;
   R Fx = Fix, Fy = Fiy;
-  // F_ads = -G_w psi(x) sum_a w_a s(x+e_a) e_a: the solid ghost row gives sum = (0, -1/2) below, (0, 1/2) above.
-  if (!P.yper) {
-    if (y == 0 && P.ybc_lo == BC_WALL) Fy += C.G_wall * 0.5f * pc;
-    if (y == P.ny - 1 && P.ybc_hi == BC_WALL) Fy -= C.G_wall * 0.5f * pc;
-  }
+  // F_ads = -G_w psi(x) sum_a w_a s(x+e_a) e_a on the y- wall, whose solid ghost row gives the sum
+  // (0, -1/2). A y+ wall is a neutral lid (the solid surfaces of Sec. IV are bottom walls).
+  if (!P.yper && y == 0 && P.ybc_lo == BC_WALL) Fy += C.G_wall * 0.5f * pc;
   const R rho = pl.p[P_RHO][i];
   if (P.buoyancy) {  // F_b = (rho - rho_ave) g (Sec. IV B)
     const R dr = rho - R(*rho_ave);
@@ -160,10 +158,12 @@ __global__ void __launch_bounds__(BY_BLOCK ? BLOCK : 2 * BLOCK)
   if (!heat) {
     R f[9];
     pull<S, R>(fsrc, C.wf, P, x, y, f);
-    flow_closure(f, P, y);
+    flow_closure(f, P, x, y, fsrc.wall);
     const R rho = pl.p[P_RHO][i];
-    collide_flow(f, rho, vx, vy, pl.p[P_FX][i], pl.p[P_FY][i], pl.p[P_Q][i], P);
+    const R Fx = pl.p[P_FX][i], Fy = pl.p[P_FY][i];
+    collide_flow(f, rho, vx, vy, Fx, Fy, pl.p[P_Q][i], P);
     pop_store<S, R>(fdst, P.N, i, f, rho, C.wf);
+    wall_force_store(fdst.wall, P, x, y, Fx, Fy);
     return;
   }
   R g[9];
@@ -324,7 +324,9 @@ template <class S, class R> static Planes<R> planes_of(const SplitBuffers& b) {
   return pl;
 }
 
-template <class S> static PopBuf<S> fbuf(const SplitBuffers& b, int k) { return PopBuf<S>{(S*)b.f[k], b.ref_f[k]}; }
+template <class S> static PopBuf<S> fbuf(const SplitBuffers& b, int k) {
+  return PopBuf<S>{(S*)b.f[k], b.ref_f[k], b.wall[k]};
+}
 template <class S> static PopBuf<S> gbuf(const SplitBuffers& b, int k) { return PopBuf<S>{(S*)b.g[k], b.ref_g[k]}; }
 
 // Role layout of k_collide per storage type (both compute the same step): roles by block for the
@@ -374,6 +376,11 @@ template <class S>
 static cudaError_t init_impl(const SplitBuffers& b, const DevParams& P, const double* rho, const double* T,
                              const double* ux, const double* uy, cudaStream_t st) {
   const unsigned nb = blocks_for(P.N);
+  for (int k = 0; k < 2; ++k)  // no force before the first step: the initial closure takes j = 0 on walls
+    if (b.wall[k]) {
+      const cudaError_t e = cudaMemsetAsync(b.wall[k], 0, wall_doubles(P.nx) * sizeof(double), st);
+      if (e != cudaSuccess) return e;
+    }
   k_init<S><<<nb, BLOCK, 0, st>>>(rho, T, ux, uy, fbuf<S>(b, 0), gbuf<S>(b, 0), P);
   // rho_ave of the initial (post-boundary) state
   k_sums<S><<<nb, BLOCK, 0, st>>>(fbuf<S>(b, 0), gbuf<S>(b, 0), P, b.partials, (int)nb);

@@ -52,7 +52,8 @@ DevParams make_dev_params_public(const lbpc_params* p);
 }
 
 LBPC_API lbpc_status lbpc_step_static(const lbpc_params* p, const void* f_in, const void* g_in, void* f_out,
-                                      void* g_out, void* phi_prev, double* rho_ave, int64_t step, void* stream) {
+                                      void* g_out, const double* wall_in, double* wall_out, void* phi_prev,
+                                      double* rho_ave, int64_t step, void* stream) {
   if (lbpc_check_params(p, nullptr, 0) != LBPC_OK) return LBPC_EINVAL;
   if (p->prec == LBPC_FP16DEV) return LBPC_EINVAL;  // FP16 storage needs reference planes this call does not take
   const long long N = (long long)p->nx * p->ny;
@@ -60,6 +61,8 @@ LBPC_API lbpc_status lbpc_step_static(const lbpc_params* p, const void* f_in, co
   if (!f_in || !g_in || !f_out || !g_out || !phi_prev || step < 0) return LBPC_EINVAL;
   if (p->buoyancy && !rho_ave) return LBPC_EINVAL;
   if (f_in == f_out || g_in == g_out) return LBPC_EINVAL;
+  const bool walls = p->flow_bc[2] == LBPC_WALL || p->flow_bc[3] == LBPC_WALL;
+  if (walls && (!wall_in || !wall_out || wall_in == wall_out)) return LBPC_EINVAL;
   if (lbpc::split_nplanes() > kPlanes) return LBPC_ECUDA;
   double* s = nullptr;
   if (scratch_on_current_device(&s) != cudaSuccess) return LBPC_ECUDA;
@@ -71,6 +74,8 @@ LBPC_API lbpc_status lbpc_step_static(const lbpc_params* p, const void* f_in, co
   b.g[0] = (void*)g_in;
   b.f[1] = f_out;
   b.g[1] = g_out;
+  b.wall[0] = walls ? (double*)wall_in : nullptr;  // read only: the step writes the other parity
+  b.wall[1] = walls ? wall_out : nullptr;
   b.phi_prev = phi_prev;
   for (int k = 0; k < lbpc::split_nplanes() && k < kPlanes; ++k) b.planes[k] = s + (long long)k * kMaxNodes;
   b.partials = s + kPlanes * kMaxNodes;

@@ -265,10 +265,8 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
     const R sy = (c21 - c01) * R(1.0 / 3.0) + (c22 + c20 - c00 - c02) * R(1.0 / 12.0);
     Fx = -C.G * pc * sx;
     Fy = -C.G * pc * sy;
-    if (!INTERIOR && !P.yper) {
-      if (y == 0 && P.ybc_lo == BC_WALL) Fy += C.G_wall * 0.5f * pc;
-      if (y == P.ny - 1 && P.ybc_hi == BC_WALL) Fy -= C.G_wall * 0.5f * pc;
-    }
+    // F_ads on the y- wall only (a y+ wall is a neutral lid)
+    if (!INTERIOR && !P.yper && y == 0 && P.ybc_lo == BC_WALL) Fy += C.G_wall * 0.5f * pc;
     const R rr = s_rho[hy][hx];
     if (P.buoyancy) {
       const R d = rr - rho_ref;
@@ -369,6 +367,7 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
     collide_heat(g[k], Tk, vx[k], vy[k], S0, P, tau_inv);
     pop_store<S, R>(fdst, P.N, i, f[k], rho[k], C.wf);
     pop_store<S, R>(gdst, P.N, i, g[k], Tk + S0, C.wg);
+    if (!INTERIOR) wall_force_store(fdst.wall, P, gx, gy, Fx[k], Fy[k]);
   }
 }
 

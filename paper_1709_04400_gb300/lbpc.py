@@ -97,7 +97,7 @@ def load_library(path: str = LIB_PATH):
         "lbpc_checkpoint_bytes": (ctypes.c_size_t, [vp]),
         "lbpc_save": (ctypes.c_int, [vp, vp, ctypes.c_size_t, ctypes.c_int]),
         "lbpc_load": (ctypes.c_int, [vp, vp, ctypes.c_size_t, ctypes.c_int]),
-        "lbpc_step_static": (ctypes.c_int, [P, vp, vp, vp, vp, vp, vp, ctypes.c_int64, vp]),
+        "lbpc_step_static": (ctypes.c_int, [P, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int64, vp]),
         "lbpc_batch_instance_bytes": (ctypes.c_size_t, [P]),
         "lbpc_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]),
         "lbpc_batch_add": (ctypes.c_int, [vp, P, vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int32)]),

@@ -31,8 +31,8 @@ BASE = dict(
     model="improved",
 )
 # G_wall of the heated-wall case: a neutral wall (no fluid-solid force beyond the edge-copy ghosts); the
-# paper's 45-degree contact angle is not calibrated. A wettable wall in a closed pool drives the vapour over
-# the strip to near vacuum after about 1800 steps under this build's wall readings.
+# paper's 45-degree contact angle is not calibrated. A wettable bottom wall (G_wall < 0) is stable too now
+# that the wall closure holds v = 0 under the adsorption force.
 HEATED_WALL_G_WALL = 0.0
 
 
@@ -111,3 +111,11 @@ def droplet_area(rho):
     lo = np.mean([rho[2, 2], rho[2, -3], rho[-3, 2], rho[-3, -3]])
     hi = rho[ny // 2, nx // 2]
     return float(np.clip((rho - lo) / (hi - lo), 0.0, 1.0).sum())
+
+
+def vapour_volume(rho, rho_v, rho_l, rows):
+    """Vapour volume in the lowest `rows` rows of a pool: sum of clip((rho_l - rho)/(rho_l - rho_v), 0, 1).
+    Below the free surface of the heated-wall pool this is the vapour formed over the heater; it is a
+    smooth function of the density, so it compares across precisions without a threshold's jumps."""
+    r = np.asarray(rho)[:rows]
+    return float(np.clip((rho_l - r) / (rho_l - rho_v), 0.0, 1.0).sum())

@@ -1,0 +1,96 @@
+"""Nucleation on the heated wall (Sec. IV B set-up, closed pool): the vapour formed over the heater,
+against the FP64 oracle, for every precision and inside a batch.
+
+The pool has the paper's domain, 150 x 300, liquid below y = 150. The bottom wall is held at T_s with
+a strip of 20 nodes at T_s + 0.3 T_c. The lid is closed, g = 3e-5 with buoyancy (rho - rho_ave) g, and
+lambda = rho c_V chi with chi = 0.06. After 1000 steps a vapour region sits on the wall over the strip.
+The observable is its volume below the free surface (workloads.vapour_volume over the lowest 120 rows),
+and the fields are compared as well. Every wall-row closure of the run sets j = -F/2 from the previous
+step's force, so the run exercises the wall-force state on every path."""
+
+import numpy as np
+import pytest
+
+from paper_1709_04400_gb300 import lbpc, workloads
+
+from .helpers import RL, RV, TC, max_rel, norm_rel, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+STEPS, ROWS = 1000, 120
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+
+    from paper_1709_04400_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def _case():
+    return workloads.heated_wall(TC, RV, RL, nx=150, ny=300, top="wall")
+
+
+@pytest.fixture(scope="module")
+def oracle_result():
+    from oracle import model
+
+    case, rho, T = _case()
+    p, s = run_oracle(case, rho, T, STEPS)
+    return model.fields(p, s)
+
+
+def _errors(got, ref):
+    vg = workloads.vapour_volume(got[0], RV, RL, ROWS)
+    vr = workloads.vapour_volume(ref[0], RV, RL, ROWS)
+    return dict(volume=abs(vg - vr) / vr, rho=max_rel(got[0], ref[0]), T=max_rel(got[3], ref[3]),
+                u=max(norm_rel(got[1], ref[1]), norm_rel(got[2], ref[2]))), vr
+
+
+# Bars (volume, rho and T, u): FP64 and DF64 at the parity bar. For FP32 and the binary16 deviation
+# storage the bars sit a few times above the measured errors (FP32: volume 8.6e-5, rho 1.2e-3, T 1.7e-5,
+# u 1.6e-4; FP16: 1.2e-4, 2.1e-3, 6.3e-5, 3.1e-3), well inside the 1 % bar of a derived observable. The
+# largest rho error sits in the thin vapour at the heater, where 1000 steps of fast interface motion
+# amplify the per-step rounding.
+BARS = {lbpc.FP64: (1e-10, 1e-10, 1e-10), lbpc.DF64: (1e-10, 1e-10, 1e-10),
+        lbpc.FP32: (1e-3, 5e-3, 1e-3), lbpc.FP16DEV: (1e-3, 1e-2, 1e-2)}
+
+
+@pytest.mark.parametrize("prec,path", [(lbpc.FP64, lbpc.PATH_SPLIT), (lbpc.DF64, lbpc.PATH_SPLIT),
+                                       (lbpc.FP32, lbpc.PATH_FUSED), (lbpc.FP16DEV, lbpc.PATH_FUSED)],
+                         ids=["fp64", "df64", "fp32", "fp16"])
+def test_vapour_over_heater_alone(oracle_result, prec, path):
+    case, rho, T = _case()
+    sim = lbpc.Simulation(lbpc.params_from_case(case, prec))
+    sim.set_path(path)
+    sim.init(rho, T)
+    sim.step(STEPS)
+    got = sim.fields()
+    sim.close()
+    err, vol = _errors(got, oracle_result)
+    print(f"heated wall 150x300, prec {prec}, {STEPS} steps: vapour volume {vol:.2f} nodes, errors {err}")
+    assert vol > 50  # a vapour region has formed
+    v_bar, f_bar, u_bar = BARS[prec]
+    assert err["volume"] <= v_bar and err["rho"] <= f_bar and err["T"] <= f_bar and err["u"] <= u_bar, err
+
+
+@pytest.mark.parametrize("prec", [lbpc.FP32, lbpc.FP16DEV], ids=["fp32", "fp16"])
+def test_vapour_over_heater_batched(oracle_result, prec):
+    """The same pool advanced inside a batch beside a droplet instance of another size."""
+    case, rho, T = _case()
+    other = workloads.droplet_evaporation(TC, RV, RL, n=96, radius=20.0, dT_ratio=0.2)
+    ps = [lbpc.params_from_case(case, prec), lbpc.params_from_case(other[0], prec)]
+    b = lbpc.Batch(prec, sum(lbpc.Batch.instance_bytes(p) for p in ps) + (64 << 20))
+    i = b.add(ps[0], rho, T)
+    b.add(ps[1], other[1], other[2])
+    b.step(STEPS)
+    b.check()
+    got = b.fields(i)
+    b.close()
+    err, vol = _errors(got, oracle_result)
+    print(f"heated wall 150x300 in a batch, prec {prec}, {STEPS} steps: errors {err}")
+    v_bar, f_bar, u_bar = BARS[prec]
+    assert err["volume"] <= v_bar and err["rho"] <= f_bar and err["T"] <= f_bar and err["u"] <= u_bar, err

@@ -51,6 +51,9 @@ def test_static_step_matches_workspace_step():
     g_a = ws[pop:pop + 9 * N * 8].view(torch.float64).clone()
     f_b = torch.empty_like(f_a)
     g_b = torch.empty_like(g_a)
+    # wall-row forces of the previous step (none before the first): [4][nx], A/B like the populations
+    wall_a = torch.zeros(4 * params.nx, dtype=torch.float64, device="cuda")
+    wall_b = torch.empty_like(wall_a)
     phi = torch.zeros(N, dtype=torch.float64, device="cuda")
     rho_ave = torch.tensor([mass0 / N], dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
@@ -58,14 +61,16 @@ def test_static_step_matches_workspace_step():
     c = params.to_c()
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
-    def static_step(fi, gi, fo, go, k):
-        return lib.lbpc_step_static(ctypes.byref(c), ctypes.c_void_p(fi.data_ptr()), ctypes.c_void_p(gi.data_ptr()),
-                                    ctypes.c_void_p(fo.data_ptr()), ctypes.c_void_p(go.data_ptr()),
-                                    ctypes.c_void_p(phi.data_ptr()), ctypes.c_void_p(rho_ave.data_ptr()), k, stream)
+    def ptr(t):
+        return ctypes.c_void_p(t.data_ptr())
+
+    def static_step(fi, gi, wi, fo, go, wo, k):
+        return lib.lbpc_step_static(ctypes.byref(c), ptr(fi), ptr(gi), ptr(fo), ptr(go), ptr(wi), ptr(wo), ptr(phi),
+                                    ptr(rho_ave), k, stream)
 
     # two calls in a row: A -> B, then B -> A
-    assert static_step(f_a, g_a, f_b, g_b, 0) == lbpc.LBPC_OK
-    assert static_step(f_b, g_b, f_a, g_a, 1) == lbpc.LBPC_OK
+    assert static_step(f_a, g_a, wall_a, f_b, g_b, wall_b, 0) == lbpc.LBPC_OK
+    assert static_step(f_b, g_b, wall_b, f_a, g_a, wall_a, 1) == lbpc.LBPC_OK
 
     sim.step(2)  # the existing entry point from the same start; its state is back in the first half
     torch.cuda.synchronize()
@@ -85,5 +90,5 @@ def test_static_step_rejects_grids_beyond_its_scratch():
     c = big.to_c()
     buf = torch.empty(16, dtype=torch.float64, device="cuda")
     p = ctypes.c_void_p(buf.data_ptr())
-    s = lib.lbpc_step_static(ctypes.byref(c), p, p, p, p, p, p, 0, ctypes.c_void_p(0))
+    s = lib.lbpc_step_static(ctypes.byref(c), p, p, p, p, p, p, p, p, 0, ctypes.c_void_p(0))
     assert s == lbpc.LBPC_ENOMEM
