@@ -149,7 +149,7 @@ template <class R> __device__ __forceinline__ void eos(R rho, R T, const DevPara
 // by the step that stored the populations: the next step's wall closure sets j = -F/2 from it.
 template <class S> struct PopBuf {
   S* p;
-  float* ref;              // FP16 storage only
+  float* ref;    // FP16 storage only
   double* wall;  // flow buffers: wall-row forces (null where unused; aggregate init leaves it null)
 };
 
@@ -196,20 +196,37 @@ __device__ __forceinline__ int wrapx(int x, int nx) { return x < 0 ? x + nx : (x
 
 // Post-stream populations at (x, y): src holds post-collision populations (SoA [9][N]); a
 // population whose source node lies beyond a non-periodic y edge is unknown and returned as 0.
+//
+// The nine source nodes (x - e_a) share three columns and three rows; PullSrc holds them once per node
+// (x, y inside the grid), wrapped on the periodic axes. Entry k of each array is the source for e = k - 1.
+struct PullSrc {
+  int col[3];  // x + 1, x, x - 1 (wrapped)
+  int row[3];  // y + 1, y, y - 1 (wrapped when y is periodic; -1 beyond a non-periodic y edge)
+};
+__device__ __forceinline__ PullSrc pull_src(const DevParams& P, int x, int y) {
+  PullSrc s;
+  s.col[0] = x == P.nx - 1 ? 0 : x + 1;
+  s.col[1] = x;
+  s.col[2] = x == 0 ? P.nx - 1 : x - 1;
+  s.row[0] = y == P.ny - 1 ? (P.yper ? 0 : -1) : y + 1;
+  s.row[1] = y;
+  s.row[2] = y == 0 ? (P.yper ? P.ny - 1 : -1) : y - 1;
+  return s;
+}
+
 template <class S, class R>
-__device__ __forceinline__ void pull(const PopBuf<S>& src, const R* w, const DevParams& P, int x, int y, R v[9]) {
+__device__ __forceinline__ void pull_from(const PopBuf<S>& src, const R* w, const DevParams& P, const PullSrc& s,
+                                          R v[9]) {
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
-    const int sx = wrapx(x - EX(a), P.nx);
-    int sy = y - EY(a);
-    if (P.yper) {
-      sy = sy < 0 ? sy + P.ny : (sy >= P.ny ? sy - P.ny : sy);
-    } else if (sy < 0 || sy >= P.ny) {
-      v[a] = R(0);
-      continue;
-    }
-    v[a] = pop_load<S, R>(src, P.N, a, (long long)sy * P.nx + sx, w);
+    const int r = s.row[EY(a) + 1];
+    v[a] = r >= 0 ? pop_load<S, R>(src, P.N, a, (long long)r * P.nx + s.col[EX(a) + 1], w) : R(0);
   }
+}
+
+template <class S, class R>
+__device__ __forceinline__ void pull(const PopBuf<S>& src, const R* w, const DevParams& P, int x, int y, R v[9]) {
+  pull_from<S, R>(src, w, P, pull_src(P, x, y), v);
 }
 
 // Zou-He closure of the unknown f on a non-periodic y edge. Wall: the momentum is set to j = -F/2, F
@@ -330,8 +347,9 @@ template <class S, class R>
 __device__ __forceinline__ void pull_closed(const PopBuf<S>& fsrc, const PopBuf<S>& gsrc, const DevParams& P, int x,
                                             int y, R f[9], R g[9]) {
   const Coefs<R>& C = coefs<R>(P);
-  pull<S, R>(fsrc, C.wf, P, x, y, f);
-  pull<S, R>(gsrc, C.wg, P, x, y, g);
+  const PullSrc src = pull_src(P, x, y);  // f and g read the same nine source nodes
+  pull_from<S, R>(fsrc, C.wf, P, src, f);
+  pull_from<S, R>(gsrc, C.wg, P, src, g);
   flow_closure(f, P, x, y, fsrc.wall);
   heat_closure(g, P, x, y);
 }
