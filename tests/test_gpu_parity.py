@@ -77,6 +77,40 @@ def test_mixed_boundaries_fp64(path, prec):
     assert np.max(np.abs(g - s.g)) / np.max(np.abs(s.g)) < 1e-10
 
 
+def _closed_wettable_pool():
+    """Both y edges are walls with a wettable bottom (G_w = -0.2), buoyancy and a hot strip: the wall
+    rows' force of the previous step enters the closure on both walls, the adsorption acts on the
+    bottom wall only, and the lid stays neutral."""
+    case, rho, T = workloads.mixed_small(TC, RV, RL, nx=45, ny=31)
+    case = dict(case, name="closed_wettable_45x31", flow_bc=("periodic", "periodic", "wall", "wall"),
+                rho_bc=(0.0,) * 4)
+    return case, rho, T
+
+
+@pytest.mark.parametrize("prec", F64, ids=F64_IDS)
+@pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
+def test_closed_pool_wettable_walls_fp64(path, prec):
+    case, rho, T = _closed_wettable_pool()
+    steps = 200
+    gpu, f, g, (mass, _) = _gpu(case, rho, T, steps, prec=prec, path=path)
+    p, s = _oracle("closed_wettable", case, rho, T, steps)
+    _assert_within(_errors(gpu, p, s), 1e-10)
+    assert np.max(np.abs(f - s.f)) / np.max(np.abs(s.f)) < 1e-10
+    assert abs(mass - s.f.sum()) / s.f.sum() < 1e-12
+
+
+# FP32: the 1e-4 bar; binary16 deviation storage: its documented bounds (rho and T 1e-3 per 100 steps,
+# u 2e-2 relative to the small velocities)
+@pytest.mark.parametrize("prec,tol,tol_u", [(lbpc.FP32, 1e-4, 1e-4), (lbpc.FP16DEV, 2e-3, 2e-2)], ids=["fp32", "fp16"])
+def test_closed_pool_wettable_walls_reduced(prec, tol, tol_u):
+    case, rho, T = _closed_wettable_pool()
+    gpu, *_ = _gpu(case, rho, T, 200, prec=prec, path=lbpc.PATH_FUSED)
+    p, s = _oracle("closed_wettable", case, rho, T, 200)
+    err = _errors(gpu, p, s)
+    print(f"closed wettable pool, prec {prec}, 200 steps: {err}")
+    assert err["rho"] <= tol and err["T"] <= tol and err["ux"] <= tol_u and err["uy"] <= tol_u, err
+
+
 @pytest.mark.parametrize("prec", F64, ids=F64_IDS)
 @pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
 @pytest.mark.parametrize("mdl", ["compromised", "gong_cheng"])
