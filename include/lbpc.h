@@ -108,8 +108,8 @@ typedef struct {
   double rho_bc[4];        /* density held on LBPC_PRESSURE edges */
   double T_bc[4];          /* temperature held on LBPC_T_DIRICHLET edges */
   double T_strip;          /* temperature of the heated strip */
-  double G_wall;           /* fluid-solid strength: F_ads = -G_wall psi(x) sum_a w_a s(x+e_a) e_a at the
-                              y- wall (G_wall < 0 wets); a y+ wall is a neutral lid */
+  double G_wall;           /* fluid-solid strength: F_ads = -G_wall psi(x) sum_a w_a psi(x) s(x+e_a) e_a at
+                              the y- wall (G_wall < 0 wets); a y+ wall is a neutral lid */
 } lbpc_params;
 
 /* Library version (LBPC_VERSION). */

@@ -27,8 +27,8 @@ READINGS (the paper is silent or delegates; every one is also listed in the desi
     forcing scheme's velocity, so j = -F/2 with the wall row's force of the step before) or a
     fixed-density edge (Zou-He, u_x = 0). Stencils that cross such an edge, F_int's included, see
     ghost rows that copy the edge row (zero gradient), so a wall with G_w = 0 is neutral; at the y-
-    wall the adsorption force F_ads = -G_w psi(x) sum_a w_a s(x + e_a) e_a (s = 1 on the solid ghost
-    row) sets the wettability (G_w < 0 attracts liquid). A y+ wall is a neutral lid: every solid
+    wall the adsorption force F_ads = -G_w psi(x) sum_a w_a psi(x) s(x + e_a) e_a (s = 1 on the solid
+    ghost row, which takes the fluid node's psi) sets the wettability (G_w < 0 attracts liquid). A y+ wall is a neutral lid: every solid
     surface of Sec. IV (the droplet on a surface, the heated wall) is the bottom one.
   * A held temperature on a non-periodic y edge (wall rows, the heated strip) enters through the
     unknown g by anti-bounce-back; without one those g bounce back (zero heat flux). A Dirichlet
@@ -231,8 +231,9 @@ def macroscopic(p: OracleParams, s: OracleState):
         Fix, Fiy = -p.G * psi * sx, -p.G * psi * sy
         ax = sum(wF[L.EX[a] ** 2 + L.EY[a] ** 2] * _nb(solid, a) * L.EX[a] for a in range(1, 9))
         ay = sum(wF[L.EX[a] ** 2 + L.EY[a] ** 2] * _nb(solid, a) * L.EY[a] for a in range(1, 9))
-        Fx = Fix - p.G_wall * psi * ax
-        Fy = Fiy - p.G_wall * psi * ay
+        # F_ads = -G_w psi(x) sum_a w_a psi(x) s(x + e_a) e_a: the solid node takes the fluid node's psi
+        Fx = Fix - p.G_wall * psi * psi * ax
+        Fy = Fiy - p.G_wall * psi * psi * ay
         if p.buoyancy:
             Fx = Fx + (rho - s.rho_ave) * p.gx
             Fy = Fy + (rho - s.rho_ave) * p.gy

@@ -116,9 +116,9 @@ __global__ void __launch_bounds__(BLOCK) k_force(Planes<R> pl, DevParams P, cons
   const R sy = (c[2][1] - c[0][1]) * R(1.0 / 3.0) + (c[2][2] + c[2][0] - c[0][0] - c[0][2]) * R(1.0 / 12.0);
   const R Fix = -C.G * pc * sx, Fiy = -C.G * pc * sy;
   R Fx = Fix, Fy = Fiy;
-  // F_ads = -G_w psi(x) sum_a w_a s(x+e_a) e_a on the y- wall, whose solid ghost row gives the sum
-  // (0, -1/2). A y+ wall is a neutral lid (the solid surfaces of Sec. IV are bottom walls).
-  if (!P.yper && y == 0 && P.ybc_lo == BC_WALL) Fy += C.G_wall * 0.5f * pc;
+  // F_ads = -G_w psi(x) sum_a w_a psi(x) s(x+e_a) e_a on the y- wall, whose solid ghost row gives the
+  // sum (0, -1/2). A y+ wall is a neutral lid (the solid surfaces of Sec. IV are bottom walls).
+  if (!P.yper && y == 0 && P.ybc_lo == BC_WALL) Fy += C.G_wall * 0.5f * pc * pc;
   const R rho = pl.p[P_RHO][i];
   if (P.buoyancy) {  // F_b = (rho - rho_ave) g (Sec. IV B)
     const R dr = rho - R(*rho_ave);

@@ -265,8 +265,8 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
     const R sy = (c21 - c01) * R(1.0 / 3.0) + (c22 + c20 - c00 - c02) * R(1.0 / 12.0);
     Fx = -C.G * pc * sx;
     Fy = -C.G * pc * sy;
-    // F_ads on the y- wall only (a y+ wall is a neutral lid)
-    if (!INTERIOR && !P.yper && y == 0 && P.ybc_lo == BC_WALL) Fy += C.G_wall * 0.5f * pc;
+    // F_ads = -G_w psi(x) sum_a w_a psi(x) s(x+e_a) e_a, on the y- wall only (a y+ wall is a neutral lid)
+    if (!INTERIOR && !P.yper && y == 0 && P.ybc_lo == BC_WALL) Fy += C.G_wall * 0.5f * pc * pc;
     const R rr = s_rho[hy][hx];
     if (P.buoyancy) {
       const R d = rr - rho_ref;
