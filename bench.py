@@ -40,6 +40,9 @@ def parse():
     ap.add_argument("--requests", type=int, default=300, help="served workload: number of requests")
     ap.add_argument("--rate", type=float, default=40.0, help="served workload: Poisson arrival rate (1/s)")
     ap.add_argument("--instances", type=int, default=256, help="batched workload: number of instances")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="batched workload: step-kernel variant 0-5 instead of the autotuner's choice")
+    ap.add_argument("--ctas", type=int, default=16, help="batched workload with --variant: CTAs per SM")
     ap.add_argument("--n", type=int, default=0, help="grid side (0 = the workload's own size)")
     ap.add_argument("--dT", type=float, default=0.1, help="superheat dT / T_c of the evaporation case")
     ap.add_argument("--prec", default="", choices=["", "fp64", "df64", "fp32", "fp16"])
@@ -216,6 +219,9 @@ MEASURED_TRAFFIC = {
     ("k_collide", "droplet_evaporation_256_dT0.1Tc", "fp64"): 14_743_040,
     ("k_fused", "droplet_evaporation_4096_dT0.1Tc", "fp32"): 2_508_914_304,
     ("k_collide", "droplet_evaporation_2048_dT0.1Tc", "df64"): 1_639_130_112,
+    # batched step, 32x8 tiles (variant 0): 147.9 B/node captured on 96 instances (9.8 M nodes; 145 B/node on
+    # 48), scaled by nodes to the 256 instances (27.1 M nodes)
+    ("k_batch_step", "batched_evaporation_256", "fp32", 0): 4_008_000_000,
 }
 
 
@@ -440,7 +446,11 @@ def run_batch(args):
     b = lbpc.Batch(prec, arena, max_instances=len(insts) + 8)
     for p, (c, r, t) in zip(params, insts):
         b.add(p, r, t)
-    tuned = b.autotune(steps_per_candidate=2)
+    if args.variant >= 0:  # a fixed configuration (no tuner launches before the timed steps)
+        b.set_config(args.variant, args.ctas)
+        tuned = {"fixed": True, "variant": args.variant, "ctas_per_sm": args.ctas}
+    else:
+        tuned = b.autotune(steps_per_candidate=2)
     b.step(args.warmup)
     b.check()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -496,7 +506,10 @@ def run_batch(args):
                        "how": "each instance stepped alone through lbpc_step (fused kernel, one launch per step)"},
         "batched_over_plain": value / plain,
         "roofline": {"bound": "hbm", "kernel": "k_batch_step", "achieved": achieved, "peak": peak_bw, "unit": "GB/s",
-                     "frac": achieved / peak_bw, "traffic": None, "bytes_per_node": fused_bytes_per_node(pb),
+                     "frac": achieved / peak_bw,
+                     "traffic": MEASURED_TRAFFIC.get(("k_batch_step", f"batched_evaporation_{args.instances}",
+                                                      prec_name, tuned.get("variant", -1))),
+                     "bytes_per_node": fused_bytes_per_node(pb),
                      "frac_of_nominal": achieved / NOMINAL_HBM_GBS},
         "gpu_launches": 2 * args.steps, "clocks": clk.summary(),
     }
