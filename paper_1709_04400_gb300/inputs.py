@@ -78,9 +78,10 @@ def droplet_hot_ring(nx, ny, radius, width, rho_l, rho_v, T_sat, dT):
     return rho, T_sat + dT * s
 
 
-def pool_with_noise(seed, nx, ny, width, rho_l, rho_v, T_sat, amp=1e-4):
-    """Liquid below y = ny/2, vapour above, plus seeded uniform density noise in [-amp, amp)."""
-    rho = tanh_layer(nx, ny, ny / 2.0, width, rho_l, rho_v)
+def pool_with_noise(seed, nx, ny, width, rho_l, rho_v, T_sat, amp=1e-4, surface=None):
+    """Liquid below y = surface (default ny/2), vapour above, plus seeded uniform density noise in
+    [-amp, amp)."""
+    rho = tanh_layer(nx, ny, ny / 2.0 if surface is None else float(surface), width, rho_l, rho_v)
     rho = rho + amp * (2.0 * uniform(seed, nx * ny).reshape(ny, nx) - 1.0)
     return rho, np.full((ny, nx), T_sat)
 

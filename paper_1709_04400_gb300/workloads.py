@@ -15,6 +15,8 @@ decides whose EOS evaluation supplies them. Nothing here evaluates the lattice B
                        top held at the vapour density and T_s, g = 3e-5 downward with buoyancy
                        (rho - rho_ave) g, lambda = rho c_V chi with chi = 0.06 (Sec. IV B).
   paper_d2_law         the paper's own D^2-law set-up (Sec. IV A): 200 x 200, D0 = 60, dT = 0.14 T_c.
+  bubble_departure     100 x 200 closed pool under a thin vapour cushion, wettable wall with a heated
+                       strip, g = 1e-4: bubbles grow, detach and repeat (Sec. IV B).
 """
 
 import numpy as np
@@ -63,6 +65,24 @@ def heated_wall(Tc, rho_v, rho_l, nx=300, ny=400, strip_width=20, dT_strip_ratio
                 flow_bc=("periodic", "periodic", "wall", top), rho_bc=(0.0, 0.0, 0.0, rho_v),
                 t_bc=("none", "none", "dirichlet", "dirichlet"), T_bc=(0.0, 0.0, Ts, Ts),
                 strip=(x0, x0 + strip_width, Ts + dT_strip_ratio * Tc), G_wall=HEATED_WALL_G_WALL)
+    return case, rho, T
+
+
+def bubble_departure(Tc, rho_v, rho_l, nx=100, ny=200, strip_width=20, dT_strip_ratio=0.3, g=1e-4,
+                     G_wall=-0.1, surface_ratio=0.85, seed=inputs.SEED_BASE + 6):
+    """Nucleate boiling with departing bubbles (Sec. IV B, closed pool): liquid below y = 0.85 ny under
+    a thin vapour cushion, a wettable bottom wall at T_s (G_wall = -0.1) with a heated strip of 20 nodes
+    at T_s + 0.3 T_c, a closed neutral lid at T_s, g = 1e-4 with buoyancy (rho - rho_ave) g, and
+    lambda = rho c_V chi with chi = 0.06. The vapour over the strip grows into a bubble, which departs
+    after about 9500 steps and leaves a small attached bubble that repeats the cycle."""
+    Ts = 0.86 * Tc
+    rho, T = inputs.pool_with_noise(seed, nx, ny, 4.0, rho_l, rho_v, Ts, amp=1e-4, surface=surface_ratio * ny)
+    x0 = nx // 2 - strip_width // 2
+    case = dict(BASE, name=f"bubble_departure_{nx}x{ny}", nx=nx, ny=ny, lambda_mode="rho_cv_chi", lam=0.0,
+                chi=0.06, gx=0.0, gy=-g, buoyancy=True, flow_bc=("periodic", "periodic", "wall", "wall"),
+                rho_bc=(0.0,) * 4, t_bc=("none", "none", "dirichlet", "dirichlet"), T_bc=(0.0, 0.0, Ts, Ts),
+                strip=(x0, x0 + strip_width, Ts + dT_strip_ratio * Tc), G_wall=G_wall,
+                surface=int(surface_ratio * ny))
     return case, rho, T
 
 

@@ -30,3 +30,19 @@ def max_rel(a, b):
 def norm_rel(a, b):
     """||a - b||_inf / ||b||_inf (for u, which vanishes pointwise)."""
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def departed_bubble(rho, surface, min_area=10):
+    """Area of the largest vapour region (rho below the mean of the coexistence densities, 4-connected)
+    in the rows under surface - 15 that no longer touches the wall row; 0 while every such region is
+    attached to the wall (or smaller than min_area)."""
+    from scipy import ndimage
+
+    r = np.asarray(rho)[: surface - 15]
+    lab, n = ndimage.label(r < 0.5 * (RL + RV))
+    best = 0
+    for j in range(1, n + 1):
+        ys = np.nonzero(lab == j)[0]
+        if ys.min() > 0 and len(ys) >= min_area:
+            best = max(best, len(ys))
+    return best
