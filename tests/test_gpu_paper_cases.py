@@ -17,7 +17,7 @@ import pytest
 
 from paper_1709_04400_gb300 import lbpc, workloads
 
-from .helpers import RL, RV, TC, oracle_params
+from .helpers import RL, RV, TC, departed_bubble, oracle_params
 
 pytestmark = pytest.mark.gpu
 
@@ -125,3 +125,30 @@ def test_heated_strip_nucleates_vapour():
         assert r[1:6, : x0 - 40].min() > 0.9 * RL and r[1:6, x1 + 40:].min() > 0.9 * RL, "far wall stays liquid"
         areas[prec] = sizes.max()
     assert abs(areas[lbpc.FP32] - areas[lbpc.FP64]) <= 0.05 * areas[lbpc.FP64], areas
+
+
+def test_departure_diameter_follows_inverse_root_of_gravity():
+    """Fig. 7: the departure diameter falls as g^(-1/2), D_d = 0.209 g^(-1/2) in the paper. The pool of
+    workloads.bubble_departure is run at g from 4e-5 to 2e-4 (a factor of 5). D_d = 2 sqrt(A/pi) of the
+    region that detaches, at the first check (every 20 steps) after it leaves the wall. The fitted
+    exponent must lie within 0.1 of -1/2 and the prefactor within 25 % of 0.209 (the contact-angle
+    scheme and the top boundary of the paper's set-up are not stated, so the prefactor can differ)."""
+    gs = [4e-5, 6e-5, 1e-4, 1.4e-4, 2e-4]
+    dd = []
+    for g in gs:
+        case, rho, T = workloads.bubble_departure(TC, RV, RL, g=g)
+        sim = lbpc.Simulation(lbpc.params_from_case(case, lbpc.FP64))
+        sim.init(rho, T)
+        area = 0
+        while not area and sim.step_count < 60000:
+            sim.step(20)
+            area = departed_bubble(sim.fields()[0], case["surface"])
+        sim.close()
+        assert area, g
+        dd.append(2.0 * np.sqrt(area / np.pi))
+    slope, lnc = np.polyfit(np.log(gs), np.log(dd), 1)
+    c_half = float(np.mean(np.array(dd) * np.sqrt(gs)))  # prefactor with the exponent fixed at -1/2
+    print(f"departure diameters {dict(zip(gs, np.round(dd, 2)))}: fit D_d = {np.exp(lnc):.3f} g^{slope:.3f}; "
+          f"with exponent -1/2, D_d = {c_half:.3f} g^-0.5 (paper 0.209)")
+    assert abs(slope + 0.5) <= 0.1
+    assert abs(c_half / 0.209 - 1.0) <= 0.25
