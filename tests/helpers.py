@@ -46,3 +46,20 @@ def departed_bubble(rho, surface, min_area=10):
         if ys.min() > 0 and len(ys) >= min_area:
             best = max(best, len(ys))
     return best
+
+
+def contact_angle(rho):
+    """Contact angle of a droplet sitting on the y = 0 wall at the centre column, in degrees, from its
+    height h and base half-width a (rho = (rho_l + rho_v)/2 located by linear interpolation along the
+    centre column and along row 1): a circular cap has tan(theta/2) = h/a."""
+    rho = np.asarray(rho)
+    mid = 0.5 * (RL + RV)
+    col = rho[:, rho.shape[1] // 2]
+    j = int(np.nonzero(col > mid)[0].max())
+    h = j + (col[j] - mid) / (col[j] - col[j + 1])
+    row = rho[1]
+    xs = np.nonzero(row > mid)[0]
+    i0, i1 = int(xs.min()), int(xs.max())
+    left = i0 - (row[i0] - mid) / (row[i0] - row[i0 - 1])
+    right = i1 + (row[i1] - mid) / (row[i1] - row[i1 + 1])
+    return float(np.degrees(2.0 * np.arctan(h / (0.5 * (right - left)))))
