@@ -129,14 +129,16 @@ def test_heated_strip_nucleates_vapour():
 
 def test_departure_diameter_follows_inverse_root_of_gravity():
     """Fig. 7: the departure diameter falls as g^(-1/2), D_d = 0.209 g^(-1/2) in the paper. The pool of
-    workloads.bubble_departure is run at g from 4e-5 to 2e-4 (a factor of 5). D_d = 2 sqrt(A/pi) of the
+    workloads.bubble_departure, with the paper's 45-degree contact angle (G_wall = -0.17 under this
+    build's adsorption force, calibrated on a sessile droplet), is run at g from 4e-5 to 2e-4 (a factor
+    of 5); measured D_d = 0.234 g^(-1/2), fitted 0.212 g^-0.511. D_d = 2 sqrt(A/pi) of the
     region that detaches, at the first check (every 20 steps) after it leaves the wall. The fitted
     exponent must lie within 0.1 of -1/2 and the prefactor within 25 % of 0.209 (the contact-angle
     scheme and the top boundary of the paper's set-up are not stated, so the prefactor can differ)."""
     gs = [4e-5, 6e-5, 1e-4, 1.4e-4, 2e-4]
     dd = []
     for g in gs:
-        case, rho, T = workloads.bubble_departure(TC, RV, RL, g=g)
+        case, rho, T = workloads.bubble_departure(TC, RV, RL, g=g, G_wall=-0.17)
         sim = lbpc.Simulation(lbpc.params_from_case(case, lbpc.FP64))
         sim.init(rho, T)
         area = 0
