@@ -29,7 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the double-word (DF64) variant of an FP64 run")
     ap.add_argument("--no-side-run", action="store_true", help="served workload: no 4096^2 FP16 run alongside")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def dist_env():
@@ -62,6 +62,24 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(values, ws, device):
+    """Element-wise maximum of per-rank timings over all ranks of the process group (the slowest
+    rank's time); the values themselves on a single rank."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def aggregate_mlups(ws, nodes, steps, seconds):
+    """Whole-job throughput: each of ws ranks advances its own replica of `nodes` nodes by `steps`
+    steps in `seconds` (the slowest rank's time)."""
+    return ws * nodes * steps / seconds / 1e6
 
 
 def make_case(args, Tc, rv, rl):
@@ -296,11 +314,8 @@ def run_native(args):
         wall = time.perf_counter() - t0
     clocks = clk.summary()
     dev_s = sum(step_ms) / 1e3
-    t_all = torch.tensor([dev_s, wall], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
-    dev_s, wall = float(t_all[0]), float(t_all[1])
-    value = ws * N * args.steps / dev_s / 1e6
+    dev_s, wall = max_over_ranks([dev_s, wall], ws, "cuda")
+    value = aggregate_mlups(ws, N, args.steps, dev_s)
     nk = len(per_kernel)
 
     # dominant kernel and its roofline
@@ -386,14 +401,11 @@ def run_native(args):
         torch.cuda.synchronize()
         barrier()
         te = time.perf_counter() - t0
-        t_e = torch.tensor([te], dtype=torch.float64, device="cuda")
-        if ws > 1:
-            dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
-        te = float(t_e[0])
+        te = max_over_ranks([te], ws, "cuda")[0]
         sim2.close()
         h2d = 2 * N * 8
         d2h = args.steps * 16 + 4 * N * 8
-        e2e = {"value": ws * N * args.steps / te / 1e6, "unit": "MLUPS",
+        e2e = {"value": aggregate_mlups(ws, N, args.steps, te), "unit": "MLUPS",
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                "note": "lbpc_init from pinned host fields, lbpc_step(1) + lbpc_sums per step, lbpc_fields to host"}
     sim.close()
