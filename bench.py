@@ -39,6 +39,9 @@ def parse(argv=None):
                     choices=["evaporation", "droplet", "heated_wall", "batch", "serve"])
     ap.add_argument("--requests", type=int, default=300, help="served workload: number of requests")
     ap.add_argument("--rate", type=float, default=40.0, help="served workload: Poisson arrival rate (1/s)")
+    ap.add_argument("--full-stream", action="store_true",
+                    help="served workload: the full request distribution (sides 64-1024, 5k-50k steps) instead of the "
+                         "bounded one (64-512, 1k-5k)")
     ap.add_argument("--instances", type=int, default=256, help="batched workload: number of instances")
     ap.add_argument("--variant", type=int, default=-1,
                     help="batched workload: step-kernel variant 0-5 instead of the autotuner's choice")
@@ -541,8 +544,11 @@ def run_serve(args):
     torch.cuda.set_device(local)
     build.build()
     prec = {"": lbpc.FP32, "fp32": lbpc.FP32, "fp16": lbpc.FP16DEV, "fp64": lbpc.FP64}[args.prec]
-    reqs = serve.poisson_stream(args.requests, rate=args.rate, seed=170904400 + 4, side_lo=64, side_hi=512,
-                                steps_lo=1000, steps_hi=5000)
+    if args.full_stream:  # the full request distribution: sides 64-1024, 5k-50k steps
+        lo_hi = dict(side_lo=64, side_hi=1024, steps_lo=5000, steps_hi=50000)
+    else:
+        lo_hi = dict(side_lo=64, side_hi=512, steps_lo=1000, steps_hi=5000)
+    reqs = serve.poisson_stream(args.requests, rate=args.rate, seed=170904400 + 4, **lo_hi)
     srv = serve.Server(prec=prec, hbm_budget_bytes=24 << 30)
 
     # the stream runs alongside one 4096 x 4096 FP16-deviation evaporation run on its own CUDA stream,
@@ -603,7 +609,8 @@ def run_serve(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if prec == lbpc.FP64 else "f32", "data": "synthetic",
                 "config": {"workload": f"served_stream_{args.requests}", "rate_per_s": args.rate,
-                           "sides": [64, 512], "steps": [1000, 5000], "mix": "half evaporation, half heated wall",
+                           "sides": [lo_hi["side_lo"], lo_hi["side_hi"]], "steps": [lo_hi["steps_lo"], lo_hi["steps_hi"]],
+                           "mix": "half evaporation, half heated wall",
                            "storage": args.prec or "fp32", "budget_gb": 24},
                 "latency": {"p50_s": st["p50_s"], "p99_s": st["p99_s"], "mean_s": st["mean_s"]},
                 "served": st, "side_run": side, "clocks": clk.summary()}

@@ -46,6 +46,7 @@ class Result:
     nodes: int
     message: str = ""
     fields: Optional[tuple] = None
+    detail: str = ""  # the library's report of a failure (step, node, cause)
 
     @property
     def time_to_result(self):
@@ -58,10 +59,13 @@ def make_case(req: Request, Tc, rho_v, rho_l):
         return workloads.droplet_evaporation(Tc, rho_v, rho_l, n=req.side, radius=req.size_param,
                                              dT_ratio=req.superheat)
     if req.kind == "heated_wall":
-        # closed pool (neutral wall): the fixed-pressure top of the benchmark set-up diverges after about
-        # 1800 steps under this build's boundary readings, and requests run for thousands of steps
+        # Closed pool (neutral wall) under a vapour cushion of at most 48 rows. An open top lets the
+        # buoyancy (rho - rho_ave) g accelerate the vapour out without bound. In a closed pool the cushion
+        # must carry a pressure difference of about (rho_ave - rho_v) g H: a half-full pool of side 734 or
+        # more takes it past the saturation pressure, and the vapour over the liquid is drawn to vacuum
+        # after about 1800 steps. 48 rows keep it under a third of p_sat at every side.
         return workloads.heated_wall(Tc, rho_v, rho_l, nx=req.side, ny=req.side, strip_width=int(req.size_param),
-                                     dT_strip_ratio=req.superheat, top="wall")
+                                     dT_strip_ratio=req.superheat, top="wall", vapour_rows=min(req.side // 2, 48))
     raise ValueError(req.kind)
 
 
@@ -126,12 +130,12 @@ class Server:
             self.pending.popleft()
             self.active[i] = [req, req.steps, now, p.nx * p.ny]
 
-    def _retire(self, now, failed_ids=()):
+    def _retire(self, now, failed_ids=(), detail=""):
         for i in list(self.active):
             req, left, adm, nodes = self.active[i]
             if i in failed_ids:
                 self.results.append(Result(req.rid, "failed", req.arrival, adm, now, req.steps - left, nodes,
-                                           "non-physical state"))
+                                           "non-physical state", detail=detail))
             elif left == 0:
                 f = self.batch.fields(i) if self.keep_fields else None
                 self.results.append(Result(req.rid, "ok", req.arrival, adm, self.clock() - self.t0, req.steps, nodes,
@@ -168,7 +172,7 @@ class Server:
                     i = getattr(e, "instance", None)
                     if e.status != lbpc.LBPC_ENONPHYS or i not in self.active:
                         raise  # not a per-instance failure: nothing to retire
-                    self._retire(self.clock() - self.t0, failed_ids={i})
+                    self._retire(self.clock() - self.t0, failed_ids={i}, detail=str(e))
             self._retire(self.clock() - self.t0)
         self.makespan = self.clock() - self.t0
         return self.results

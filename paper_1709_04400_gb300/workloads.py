@@ -55,10 +55,12 @@ def droplet_evaporation(Tc, rho_v, rho_l, n=256, radius=40.0, dT_ratio=0.1):
 
 
 def heated_wall(Tc, rho_v, rho_l, nx=300, ny=400, strip_width=20, dT_strip_ratio=0.3, g=3e-5,
-                seed=inputs.SEED_BASE + 2, top="pressure"):
-    """top = "pressure" holds the vapour density (the fixed-pressure top); "wall" closes the pool."""
+                seed=inputs.SEED_BASE + 2, top="pressure", vapour_rows=None):
+    """top = "pressure" holds the vapour density (the fixed-pressure top); "wall" closes the pool.
+    vapour_rows = None fills the pool to ny/2; a number leaves that many vapour rows under the top."""
     Ts = 0.86 * Tc
-    rho, T = inputs.pool_with_noise(seed, nx, ny, 4.0, rho_l, rho_v, Ts, amp=1e-4)
+    surface = None if vapour_rows is None else ny - vapour_rows
+    rho, T = inputs.pool_with_noise(seed, nx, ny, 4.0, rho_l, rho_v, Ts, amp=1e-4, surface=surface)
     x0 = nx // 2 - strip_width // 2
     case = dict(BASE, name=f"heated_wall_{nx}x{ny}" + ("" if top == "pressure" else "_closed"), nx=nx, ny=ny,
                 lambda_mode="rho_cv_chi", lam=0.0, chi=0.06, gx=0.0, gy=-g, buoyancy=True,
