@@ -185,6 +185,15 @@ lbpc_status lbpc_fields(lbpc_ctx* c, double* rho, double* ux, double* uy, double
  * fixed order. Synchronises the stream. */
 lbpc_status lbpc_sums(lbpc_ctx* c, double* mass, double* heat);
 
+/* The same sums without waiting: enqueues their kernels and a copy of {mass, heat} (two doubles) into
+ * out on the context's stream and returns. out is pinned host memory (on_device = 0; pageable memory
+ * also works, with a synchronous copy) or device memory (on_device = 1), owned by the caller and valid
+ * until the stream has passed the copy (lbpc_check, or a synchronisation of the stream). A per-step
+ * read of the result that keeps the stream busy. Returns LBPC_EINVAL for a null pointer,
+ * LBPC_ESTATE before lbpc_init, LBPC_ECUDA if a launch fails; device-side errors surface at the next
+ * lbpc_check / lbpc_step. */
+lbpc_status lbpc_sums_async(lbpc_ctx* c, double* out, int on_device);
+
 /* Checkpoint / resume. The paper has no counterpart; this is plumbing for long runs and for a
  * service that moves or pre-empts simulations.
  *

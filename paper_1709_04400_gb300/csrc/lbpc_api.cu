@@ -681,6 +681,18 @@ LBPC_API lbpc_status lbpc_sums(lbpc_ctx* c, double* mass, double* heat) {
   return LBPC_OK;
 }
 
+LBPC_API lbpc_status lbpc_sums_async(lbpc_ctx* c, double* out, int on_device) {
+  lbpc::TraceRange trace_("lbpc_sums_async");
+  if (!c || !out) return LBPC_EINVAL;
+  if (!c->initialised) return LBPC_ESTATE;
+  DeviceGuard g(c->device);
+  CU(c, lbpc::split_sums(c->buf, c->dp, c->p.prec, c->cur, c->stream), "lbpc_sums_async kernels");
+  CU(c, cudaMemcpyAsync(out, c->buf.scalars + 1, 2 * sizeof(double),
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream),
+     "lbpc_sums_async copy");
+  return LBPC_OK;
+}
+
 LBPC_API lbpc_status lbpc_populations(lbpc_ctx* c, double* f, double* g, int on_device) {
   lbpc::TraceRange trace_("lbpc_populations");
   if (!c) return LBPC_EINVAL;

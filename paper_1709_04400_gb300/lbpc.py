@@ -28,7 +28,7 @@ PATH_AUTO, PATH_SPLIT, PATH_FUSED = 0, 1, 2
 
 EXPORTED = ["lbpc_version", "lbpc_check_params", "lbpc_workspace_bytes", "lbpc_eos_critical", "lbpc_coexistence",
             "lbpc_create", "lbpc_init", "lbpc_step", "lbpc_step_async", "lbpc_check", "lbpc_fields", "lbpc_sums",
-            "lbpc_populations", "lbpc_step_count", "lbpc_last_error", "lbpc_destroy", "lbpc_step_timed",
+            "lbpc_sums_async", "lbpc_populations", "lbpc_step_count", "lbpc_last_error", "lbpc_destroy", "lbpc_step_timed",
             "lbpc_kernel_name", "lbpc_set_path", "lbpc_step_static", "lbpc_batch_instance_bytes", "lbpc_batch_create",
             "lbpc_batch_add", "lbpc_batch_remove", "lbpc_batch_step", "lbpc_batch_check", "lbpc_batch_fields",
             "lbpc_batch_sums", "lbpc_batch_step_count", "lbpc_batch_set_config", "lbpc_batch_config",
@@ -85,6 +85,7 @@ def load_library(path: str = LIB_PATH):
         "lbpc_check": (ctypes.c_int, [vp]),
         "lbpc_fields": (ctypes.c_int, [vp, vp, vp, vp, vp, ctypes.c_int]),
         "lbpc_sums": (ctypes.c_int, [vp, dp, dp]),
+        "lbpc_sums_async": (ctypes.c_int, [vp, vp, ctypes.c_int]),
         "lbpc_populations": (ctypes.c_int, [vp, vp, vp, ctypes.c_int]),
         "lbpc_step_count": (ctypes.c_int64, [vp]),
         "lbpc_last_error": (ctypes.c_char_p, [vp]),
@@ -305,6 +306,12 @@ class Simulation:
             s = self.lib.lbpc_fields(self.ctx, *[_ptr(a) for a in out], 0)
         self._raise(s, "lbpc_fields")
         return tuple(out)
+
+    def sums_async(self, out):
+        """Enqueue the domain sums and a copy of (mass, heat) into out, a 2-element float64 CUDA tensor
+        or pinned host tensor, without waiting (lbpc_sums_async)."""
+        self._raise(self.lib.lbpc_sums_async(self.ctx, ctypes.c_void_p(out.data_ptr()), int(out.is_cuda)),
+                    "lbpc_sums_async")
 
     def sums(self):
         m, h = ctypes.c_double(), ctypes.c_double()

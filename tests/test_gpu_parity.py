@@ -304,3 +304,29 @@ def test_fused_tile_shapes(prec):
             p, s = run_oracle(case, rho, T, 60)
             for o in out:
                 _assert_within(_errors(o, p, s), 1e-4)
+
+
+def test_sums_async_equals_sums():
+    """lbpc_sums_async leaves each step's (mass, heat) in pinned host or device memory without waiting;
+    the values equal, bit for bit, lbpc_sums at the same steps of an identical context."""
+    import torch
+
+    case, rho, T = workloads.mixed_small(TC, RV, RL)
+    a = lbpc.Simulation(lbpc.params_from_case(case))
+    b = lbpc.Simulation(lbpc.params_from_case(case))
+    a.init(rho, T)
+    b.init(rho, T)
+    host = torch.zeros((5, 2), dtype=torch.float64).pin_memory()
+    dev = torch.zeros(2, dtype=torch.float64, device="cuda")
+    want = []
+    for k in range(5):
+        a.step(2, sync=False)
+        a.sums_async(host[k])
+        b.step(2)
+        want.append(list(b.sums()))
+    a.sums_async(dev)
+    a.check()
+    assert host.tolist() == want
+    assert dev.cpu().tolist() == want[-1]
+    a.close()
+    b.close()
