@@ -7,14 +7,17 @@ forcing scheme's velocity v = (j + F/2)/rho vanishes on the wall row).
   A wrong sign or factor in the tangential target fails it too.
 - A liquid at rest on a wettable wall (adsorption force normal to the wall row), in a closed box with
   gravity, keeps its mass. A closure with j = 0 moves the liquid through the wall at F/(2 rho) and
-  drains the box: about 0.4 mass units per step here, the whole mass in 1600 steps."""
+  drains the box: about 0.4 mass units per step here, the whole mass in 1600 steps.
+- A sessile droplet meets a wall without adsorption at 90 degrees, and the adsorption force moves the
+  angle the right way: above 90 for G_w > 0, below for G_w < 0."""
 
 import numpy as np
+import pytest
 
 from oracle import model
 from paper_1709_04400_gb300 import inputs
 
-from .helpers import RL, RV, TS
+from .helpers import RL, RV, TS, contact_angle
 
 
 def test_plane_poiseuille_between_walls():
@@ -49,3 +52,20 @@ def test_wettable_wall_keeps_the_liquid():
     assert abs(m3000 - m2000) <= 1e-4 * m0
     # F_y / (2 rho) on the wall row is about 1.6e-2; the wall row is at rest to the transient's decay
     assert np.max(np.abs(uy[0])) <= 1e-6
+
+
+@pytest.mark.parametrize("G_wall,lo,hi", [(0.0, 87.0, 93.0), (0.1, 105.0, 125.0), (-0.1, 55.0, 75.0)],
+                         ids=["neutral", "repelling", "wetting"])
+def test_sessile_droplet_contact_angle(G_wall, lo, hi):
+    """A droplet (r = 15) on the y- wall of an 80 x 50 box, isothermal, after 2000 steps. A wall
+    without adsorption, whose ghost row copies the edge row, meets the interface at 90 degrees. G_w > 0
+    repels the liquid (angle above 90: 113.7 here) and G_w < 0 attracts it (66.6 here). A sign error or
+    a dropped factor in F_ads fails one of the three."""
+    nx, ny = 80, 50
+    rho = inputs.tanh_droplet(nx, ny, 15.0, 4.0, RL, RV, cx=nx / 2.0, cy=4.0)
+    p = model.OracleParams(nx=nx, ny=ny, flow_bc=("periodic", "periodic", "wall", "pressure"), rho_bc=(0, 0, 0, RV),
+                           t_bc=("none", "none", "dirichlet", "dirichlet"), T_bc=(0, 0, TS, TS), G_wall=G_wall,
+                           lambda_mode="rho_cv_chi", chi=0.08)
+    s = model.run(p, model.init_state(p, rho, np.full((ny, nx), TS)), 2000)
+    theta = contact_angle(model.fields(p, s)[0])
+    assert lo <= theta <= hi, theta
