@@ -63,3 +63,20 @@ def contact_angle(rho):
     left = i0 - (row[i0] - mid) / (row[i0] - row[i0 - 1])
     right = i1 + (row[i1] - mid) / (row[i1] - row[i1 + 1])
     return float(np.degrees(2.0 * np.arctan(h / (0.5 * (right - left)))))
+
+
+def poison_byte_buffers(monkeypatch):
+    """Make torch.empty fill every uint8 buffer with 0xFF bytes: NaN in binary16, binary32 and binary64.
+    Context workspaces and batch arenas are uint8 buffers, so a kernel that reads a byte the library
+    never wrote turns its result into NaN."""
+    import torch
+
+    real_empty = torch.empty
+
+    def empty(*args, **kwargs):
+        t = real_empty(*args, **kwargs)
+        if kwargs.get("dtype") == torch.uint8:
+            t.fill_(255)
+        return t
+
+    monkeypatch.setattr(torch, "empty", empty)

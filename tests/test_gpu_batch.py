@@ -10,7 +10,7 @@ import pytest
 
 from paper_1709_04400_gb300 import inputs, lbpc, workloads
 
-from .helpers import RL, RV, TC, TS, max_rel, norm_rel, run_oracle
+from .helpers import RL, RV, TC, TS, max_rel, norm_rel, poison_byte_buffers, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -185,3 +185,31 @@ def test_failed_instance_named_and_others_unaffected():
         for a, ex in zip(b.fields(i), _solo(c, r, t, 12, prec)):
             assert np.array_equal(a, ex), c["name"]
     b.close()
+
+
+@pytest.mark.parametrize("prec", [lbpc.FP32, lbpc.FP16DEV, lbpc.FP64], ids=["fp32", "fp16", "fp64"])
+def test_no_read_of_unwritten_arena(monkeypatch, prec):
+    """The arena filled with 0xFF bytes (NaN in every storage type) before the batch is created: every
+    byte the library does not write itself stays NaN. The batch of mixed instances must step to the same
+    bits as in an ordinary arena, with the default and a tuned configuration."""
+    cases = _cases()
+
+    def run(tune):
+        b = lbpc.Batch(prec, _arena_for(cases, prec))
+        ids = [b.add(lbpc.params_from_case(c, prec), r, t) for c, r, t in cases]
+        if tune:
+            b.set_config(3, 8)
+        b.step(20)
+        b.check()
+        out = [b.fields(i) for i in ids]
+        b.close()
+        return out
+
+    for tune in (False, True):
+        clean = run(tune)
+        with monkeypatch.context() as m:
+            poison_byte_buffers(m)
+            dirty = run(tune)
+        for fc, fd in zip(clean, dirty):
+            for a, b in zip(fc, fd):
+                assert np.array_equal(a, b), tune

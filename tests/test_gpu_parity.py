@@ -11,7 +11,7 @@ import pytest
 from oracle import model
 from paper_1709_04400_gb300 import lbpc, workloads
 
-from .helpers import RL, RV, TC, TS, max_rel, norm_rel, oracle_params, run_oracle
+from .helpers import RL, RV, TC, TS, max_rel, norm_rel, oracle_params, poison_byte_buffers, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -330,3 +330,33 @@ def test_sums_async_equals_sums():
     assert dev.cpu().tolist() == want[-1]
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec,path", [(lbpc.FP64, lbpc.PATH_SPLIT), (lbpc.FP64, lbpc.PATH_FUSED),
+                                       (lbpc.DF64, lbpc.PATH_SPLIT), (lbpc.FP32, lbpc.PATH_FUSED),
+                                       (lbpc.FP32, lbpc.PATH_SPLIT), (lbpc.FP16DEV, lbpc.PATH_FUSED)],
+                         ids=["fp64-split", "fp64-fused", "df64-split", "fp32-fused", "fp32-split", "fp16-fused"])
+def test_no_read_of_unwritten_workspace(monkeypatch, prec, path):
+    """Every workspace byte the library does not write itself is NaN (0xFF): the dead population half,
+    the scratch planes, phi_prev before the first step, the partial sums. Stepping must give, bit for bit,
+    the result of an ordinary workspace. Grids: a ragged 101 x 75 pool with walls, a strip, a pressure top
+    and buoyancy, and the closed wettable pool."""
+    cases = [workloads.mixed_small(TC, RV, RL, nx=101, ny=75), _closed_wettable_pool()]
+    for case, rho, T in cases:
+        clean, fc, gc, sc = _gpu(case, rho, T, 7, prec=prec, path=path)
+        with monkeypatch.context() as m:
+            poison_byte_buffers(m)
+            dirty, fd, gd, sd = _gpu(case, rho, T, 7, prec=prec, path=path)
+        for a, b in zip(clean, dirty):
+            assert np.array_equal(a, b), case["name"]
+        assert np.array_equal(fc, fd) and np.array_equal(gc, gd) and sc == sd, case["name"]
+
+
+def test_poisoning_reaches_the_workspace(monkeypatch):
+    """The poisoned workspace of the test above really holds NaN bytes after lbpc_init (in its dead half)."""
+    case, rho, T = workloads.mixed_small(TC, RV, RL)
+    poison_byte_buffers(monkeypatch)
+    sim = lbpc.Simulation(lbpc.params_from_case(case))
+    sim.init(rho, T)
+    assert int((sim.workspace == 255).sum()) > 0
+    sim.close()
