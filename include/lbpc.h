@@ -92,7 +92,11 @@ typedef struct {
   int32_t prec;            /* lbpc_prec */
   int32_t model;           /* lbpc_thermal_model */
   int32_t lambda_mode;     /* lbpc_lambda_mode */
-  int32_t buoyancy;        /* nonzero: add F_b = (rho - rho_ave) g (Sec. IV B) */
+  int32_t buoyancy;        /* 0: no body force. 1: F_b = (rho - rho_ave) g with rho_ave the domain mean of the
+                              previous step (Sec. IV B; its total vanishes in a closed or periodic domain).
+                              2: F_b = (rho - rho_bc[3]) g, the reference being the density held on a
+                              LBPC_PRESSURE y+ edge: under an open top the vapour there is force-free, where
+                              mode 1 accelerates it out without bound. Other values: LBPC_EINVAL */
   int32_t flow_bc[4];      /* lbpc_flow_bc per edge */
   int32_t t_bc[4];         /* lbpc_thermal_bc per edge */
   int32_t strip_x0, strip_x1; /* heated strip [x0, x1) on the y- row at T_strip (needs t_bc[2]); x0 = x1: none */
@@ -330,7 +334,7 @@ void lbpc_batch_destroy(lbpc_batch* b);
  *   phi_prev  device [ny][nx] of the arithmetic type: phi of the previous step in, this step's out
  *             (ignored on input when step == 0)
  *   rho_ave   device pointer to one double: the previous step's domain mean of rho in, this step's
- *             out; used and updated only with buoyancy (may be NULL without it)
+ *             out; used and updated only with buoyancy 1 (may be NULL otherwise)
  *   step      index of this step (0 = first step after the equilibrium start)
  *   stream    cudaStream_t the work runs on; the call synchronises it before returning
  * Returns LBPC_OK, LBPC_ENONPHYS if a node left the EOS range, LBPC_EINVAL, LBPC_ENOMEM or

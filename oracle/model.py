@@ -4,7 +4,8 @@ Order of one step (Sec. III B, summary after Eq. 55; the flow model is delegated
 
   1. moments       rho = sum f, j = sum e f, T = sum g
   2. EOS           p_EOS, (dp/dT)_rho (Eq. 56); psi (READING: psi^2 = 2 (p_EOS - rho/3) / G)
-  3. force         F = F_int + F_ads + F_b  (F_b = (rho - rho_ave) g, Sec. IV B)
+  3. force         F = F_int + F_ads + F_b  (F_b = (rho - rho_ave) g, Sec. IV B; optionally, under an
+                   open top, F_b = (rho - rho_top) g with rho_top the density held there)
   4. velocity      v = (j + F/2) / rho
   5. gradients     isotropic differences for grad T, lap T, grad rho, div v (after Eq. 55)
   6. source        phi (Eq. 28, underlined terms), S0 = phi + 0.5 d_t phi (Eq. 46), backward difference
@@ -76,7 +77,7 @@ class OracleParams:
     cV: float = 5.0
     gx: float = 0.0
     gy: float = 0.0
-    buoyancy: bool = False
+    buoyancy: int = 0  # 0 none; 1 (or True): reference rho_ave; 2: reference rho_bc of the y+ pressure edge
     flow_bc: Tuple[str, str, str, str] = ("periodic",) * 4  # x-, x+, y-, y+: periodic | wall | pressure
     rho_bc: Tuple[float, float, float, float] = (0.0,) * 4
     t_bc: Tuple[str, str, str, str] = ("none",) * 4  # none | dirichlet
@@ -95,6 +96,8 @@ class OracleParams:
             raise ValueError("y edges must be both periodic or both non-periodic")
         if self.strip is not None and self.t_bc[2] != "dirichlet":
             raise ValueError("a heated strip needs a Dirichlet y- edge")
+        if int(self.buoyancy) not in (0, 1, 2) or (int(self.buoyancy) == 2 and self.flow_bc[3] != "pressure"):
+            raise ValueError("buoyancy is 0, 1, or 2 with a pressure y+ edge")
         if self.model not in ("improved", "compromised", "gong_cheng"):
             raise ValueError(self.model)
 
@@ -235,8 +238,10 @@ def macroscopic(p: OracleParams, s: OracleState):
         Fx = Fix - p.G_wall * psi * psi * ax
         Fy = Fiy - p.G_wall * psi * psi * ay
         if p.buoyancy:
-            Fx = Fx + (rho - s.rho_ave) * p.gx
-            Fy = Fy + (rho - s.rho_ave) * p.gy
+            # F_b = (rho - rho_ref) g: rho_ref = rho_ave (Sec. IV B), or for an open top the density it holds
+            rho_ref = p.rho_bc[3] if p.buoyancy == 2 else s.rho_ave
+            Fx = Fx + (rho - rho_ref) * p.gx
+            Fy = Fy + (rho - rho_ref) * p.gy
         if p.body_force is not None:
             Fx = Fx + rho * p.body_force[0]
             Fy = Fy + rho * p.body_force[1]

@@ -172,7 +172,7 @@ DevParams make_dev_params(const lbpc_params* p) {
   d.strip_x1 = p->strip_x1;
   d.model = p->model;
   d.lambda_mode = p->lambda_mode;
-  d.buoyancy = p->buoyancy != 0;
+  d.buoyancy = p->buoyancy;  // 0 none, 1 reference rho_ave, 2 reference rho_bc of the y+ edge
   d.heat_unit_rates = 1;
   for (int k = 1; k < 9; ++k) d.heat_unit_rates &= p->s_g[k] == 1.0;
   fill_coefs(d.cd, p);
@@ -267,6 +267,8 @@ LBPC_API lbpc_status lbpc_check_params(const lbpc_params* p, char* msg, size_t n
   if (p->lambda_mode == LBPC_LAMBDA_CONST && !(p->lambda > 0)) BAD("lambda must be > 0");
   if (p->lambda_mode == LBPC_LAMBDA_RHO_CV_CHI && !(p->chi > 0)) BAD("chi must be > 0");
   if (!isfinite(p->sigma) || !isfinite(p->gx) || !isfinite(p->gy) || !isfinite(p->G_wall)) BAD("non-finite parameter");
+  if (p->buoyancy < 0 || p->buoyancy > 2) BAD("buoyancy %d unknown", p->buoyancy);
+  if (p->buoyancy == 2 && p->flow_bc[3] != LBPC_PRESSURE) BAD("buoyancy 2 needs a fixed-density y+ edge");
   set_msg(msg, n, "ok");
   return LBPC_OK;
 #undef BAD
@@ -417,7 +419,7 @@ static cudaError_t launch_step(lbpc_ctx* c, cudaEvent_t* ev) {
 }
 
 static int step_kernel_count(const lbpc_ctx* c) {
-  return use_fused(c) ? (c->dp.buoyancy ? 2 : 1) : lbpc::split_kernel_count(c->dp);
+  return use_fused(c) ? (c->dp.buoyancy == 1 ? 2 : 1) : lbpc::split_kernel_count(c->dp);
 }
 
 static const char* step_kernel_name(const lbpc_ctx* c, int k) {

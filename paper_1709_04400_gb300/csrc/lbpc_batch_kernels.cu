@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(128) k_batch_advance(BatchInst<S>* __restrict_
   __shared__ double red[4];
   BatchInst<S>& I = insts[blockIdx.x];
   if (!I.active) return;
-  if (I.P.buoyancy) {
+  if (I.P.buoyancy == 1) {  // rho_ave for the next step
     double acc = 0.0;
     for (int j = threadIdx.x; j < I.ntiles; j += 128) acc += I.partials[j];
     acc = block_sum<128>(acc, red);

@@ -92,7 +92,7 @@ static cudaError_t fused_impl(const SplitBuffers& b, const DevParams& P, int cur
     k_fused<S, R, TX, TY, NPT><<<grid, TX * TY / NPT, 0, st>>>(fs, gs, fd, gd, (R*)b.phi_prev, P, step, step == 0,
                                                                b.scalars, b.partials, b.status);
   if (ev) cudaEventRecord(ev[1], st);
-  if (P.buoyancy) {
+  if (P.buoyancy == 1) {
     fused_finish(b, P, (int)(grid.x * grid.y), st);
     if (ev) cudaEventRecord(ev[2], st);
   }

@@ -120,8 +120,8 @@ __global__ void __launch_bounds__(BLOCK) k_force(Planes<R> pl, DevParams P, cons
   // sum (0, -1/2). A y+ wall is a neutral lid (the solid surfaces of Sec. IV are bottom walls).
   if (!P.yper && y == 0 && P.ybc_lo == BC_WALL) Fy += C.G_wall * 0.5f * pc * pc;
   const R rho = pl.p[P_RHO][i];
-  if (P.buoyancy) {  // F_b = (rho - rho_ave) g (Sec. IV B)
-    const R dr = rho - R(*rho_ave);
+  if (P.buoyancy) {  // F_b = (rho - rho_ref) g: rho_ref = rho_ave (Sec. IV B) or the y+ edge's held density
+    const R dr = rho - (P.buoyancy == 1 ? R(*rho_ave) : C.rho_bc_hi);
     Fx += dr * C.gx;
     Fy += dr * C.gy;
   }
@@ -339,7 +339,7 @@ static cudaError_t step_impl(const SplitBuffers& b, const DevParams& P, int cur,
   const unsigned nb = blocks_for(P.N);
   Planes<R> pl = planes_of<S, R>(b);
   if (ev) cudaEventRecord(ev[0], st);
-  k_macro<S, R><<<nb, BLOCK, 0, st>>>(fbuf<S>(b, cur), gbuf<S>(b, cur), pl, P, step, P.buoyancy, b.partials, b.status);
+  k_macro<S, R><<<nb, BLOCK, 0, st>>>(fbuf<S>(b, cur), gbuf<S>(b, cur), pl, P, step, P.buoyancy == 1, b.partials, b.status);
   if (ev) cudaEventRecord(ev[1], st);
   k_force<R><<<nb, BLOCK, 0, st>>>(pl, P, b.scalars);
   if (ev) cudaEventRecord(ev[2], st);
@@ -350,7 +350,7 @@ static cudaError_t step_impl(const SplitBuffers& b, const DevParams& P, int cur,
     k_collide<S, R, false><<<nb, 2 * BLOCK, 0, st>>>(fbuf<S>(b, cur), gbuf<S>(b, cur), fbuf<S>(b, cur ^ 1),
                                                     gbuf<S>(b, cur ^ 1), pl, (R*)b.phi_prev, P, step == 0);
   if (ev) cudaEventRecord(ev[3], st);
-  if (P.buoyancy) {
+  if (P.buoyancy == 1) {
     k_finish<<<1, BLOCK, 0, st>>>(b.partials, (int)nb, 0, 1, 1.0 / (double)P.N, b.scalars);
     if (ev) cudaEventRecord(ev[4], st);
   }
@@ -365,7 +365,7 @@ cudaError_t split_step(const SplitBuffers& b, const DevParams& P, int prec, int 
   return step_impl<__half, float>(b, P, cur, step, st, ev);
 }
 
-int split_kernel_count(const DevParams& P) { return P.buoyancy ? 4 : 3; }
+int split_kernel_count(const DevParams& P) { return P.buoyancy == 1 ? 4 : 3; }
 
 const char* split_kernel_name(int k) {
   static const char* names[] = {"k_macro", "k_force", "k_collide", "k_finish"};

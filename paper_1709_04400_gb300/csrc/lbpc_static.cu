@@ -59,7 +59,7 @@ LBPC_API lbpc_status lbpc_step_static(const lbpc_params* p, const void* f_in, co
   const long long N = (long long)p->nx * p->ny;
   if (N > kMaxNodes) return LBPC_ENOMEM;  // beyond the static scratch: use lbpc_create with a workspace
   if (!f_in || !g_in || !f_out || !g_out || !phi_prev || step < 0) return LBPC_EINVAL;
-  if (p->buoyancy && !rho_ave) return LBPC_EINVAL;
+  if (p->buoyancy == 1 && !rho_ave) return LBPC_EINVAL;
   if (f_in == f_out || g_in == g_out) return LBPC_EINVAL;
   const bool walls = p->flow_bc[2] == LBPC_WALL || p->flow_bc[3] == LBPC_WALL;
   if (walls && (!wall_in || !wall_out || wall_in == wall_out)) return LBPC_EINVAL;

@@ -241,7 +241,7 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
     s_jx[hy][hx] = fr[1] - fr[3] + fr[5] - fr[6] - fr[7] + fr[8];
     s_jy[hy][hx] = fr[2] - fr[4] + fr[5] + fr[6] - fr[7] - fr[8];
   }
-  if (P.buoyancy) {
+  if (P.buoyancy == 1) {
     double own = 0.0;
 #pragma unroll
     for (int k = 0; k < NPT; ++k) own += active[k] ? (double)rho[k] : 0.0;
@@ -254,7 +254,7 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
   // ---- stage 2: F and v on tile + 1 ----
   // F at stage-2 position (vx_, vy_) of the domain node (x, y); the stencil rows come from the clamped
   // node's own region rows so a ghost position reproduces the edge node exactly.
-  const R rho_ref = P.buoyancy ? R(*rho_ave) : R(0);
+  const R rho_ref = P.buoyancy == 1 ? R(*rho_ave) : (P.buoyancy == 2 ? C.rho_bc_hi : R(0));
   auto force_at = [&](int hx, int hy, int y, R& Fx, R& Fy, R& Q, R& vx, R& vy) {
     // hx, hy: stage-1 region coordinates of the node whose F is computed
     const R c00 = s_psi[hy - 1][hx - 1], c01 = s_psi[hy - 1][hx], c02 = s_psi[hy - 1][hx + 1];

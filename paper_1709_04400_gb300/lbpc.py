@@ -151,7 +151,7 @@ class Params:
     cV: float = 5.0
     gx: float = 0.0
     gy: float = 0.0
-    buoyancy: bool = False
+    buoyancy: int = 0  # 0 none, 1 (or True) F_b = (rho - rho_ave) g, 2 F_b = (rho - rho_bc[3]) g
     flow_bc: Sequence[int] = (PERIODIC,) * 4
     rho_bc: Sequence[float] = (0.0,) * 4
     t_bc: Sequence[int] = (T_NONE,) * 4
@@ -167,7 +167,7 @@ class Params:
     def to_c(self) -> CParams:
         c = CParams()
         c.nx, c.ny, c.prec, c.model = self.nx, self.ny, self.prec, self.model
-        c.lambda_mode, c.buoyancy = self.lambda_mode, int(bool(self.buoyancy))
+        c.lambda_mode, c.buoyancy = self.lambda_mode, int(self.buoyancy)  # True -> 1 (rho_ave), 2: top density
         c.flow_bc[:] = list(self.flow_bc)
         c.t_bc[:] = list(self.t_bc)
         if self.strip is not None:

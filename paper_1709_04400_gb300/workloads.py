@@ -12,8 +12,8 @@ decides whose EOS evaluation supplies them. Nothing here evaluates the lattice B
                        (dT / T_c in {0.05, 0.1, 0.2}); periodic flow; lambda = 2/3 (Sec. IV A).
   heated_wall          300 x 400 pool (liquid below y = 200, vapour above, density noise +-1e-4),
                        no-slip bottom wall at T_s with a heated strip 20 nodes wide at T_s + 0.3 T_c,
-                       top held at the vapour density and T_s, g = 3e-5 downward with buoyancy
-                       (rho - rho_ave) g, lambda = rho c_V chi with chi = 0.06 (Sec. IV B).
+                       top held at the vapour density and T_s, g = 3e-5 downward with buoyancy relative
+                       to the top's density, lambda = rho c_V chi with chi = 0.06 (Sec. IV B).
   paper_d2_law         the paper's own D^2-law set-up (Sec. IV A): 200 x 200, D0 = 60, dT = 0.14 T_c.
   bubble_departure     100 x 200 closed pool under a thin vapour cushion, wettable wall with a heated
                        strip, g = 1e-4: bubbles grow, detach and repeat (Sec. IV B).
@@ -55,18 +55,24 @@ def droplet_evaporation(Tc, rho_v, rho_l, n=256, radius=40.0, dT_ratio=0.1):
 
 
 def heated_wall(Tc, rho_v, rho_l, nx=300, ny=400, strip_width=20, dT_strip_ratio=0.3, g=3e-5,
-                seed=inputs.SEED_BASE + 2, top="pressure", vapour_rows=None):
+                seed=inputs.SEED_BASE + 2, top="pressure", vapour_rows=None, buoyancy=None, G_wall=None):
     """top = "pressure" holds the vapour density (the fixed-pressure top); "wall" closes the pool.
-    vapour_rows = None fills the pool to ny/2; a number leaves that many vapour rows under the top."""
+    vapour_rows = None fills the pool to ny/2; a number leaves that many vapour rows under the top.
+    buoyancy = 1 takes F_b = (rho - rho_ave) g (Sec. IV B); 2, with the pressure top, takes the density
+    held there as the reference, under which an open top stays at rest. None: 2 under the pressure top
+    (with 1 its vapour is pushed out and the run fails after about 1850 steps), 1 in a closed pool."""
+    if buoyancy is None:
+        buoyancy = 2 if top == "pressure" else 1
     Ts = 0.86 * Tc
     surface = None if vapour_rows is None else ny - vapour_rows
     rho, T = inputs.pool_with_noise(seed, nx, ny, 4.0, rho_l, rho_v, Ts, amp=1e-4, surface=surface)
     x0 = nx // 2 - strip_width // 2
     case = dict(BASE, name=f"heated_wall_{nx}x{ny}" + ("" if top == "pressure" else "_closed"), nx=nx, ny=ny,
-                lambda_mode="rho_cv_chi", lam=0.0, chi=0.06, gx=0.0, gy=-g, buoyancy=True,
+                lambda_mode="rho_cv_chi", lam=0.0, chi=0.06, gx=0.0, gy=-g, buoyancy=buoyancy,
                 flow_bc=("periodic", "periodic", "wall", top), rho_bc=(0.0, 0.0, 0.0, rho_v),
                 t_bc=("none", "none", "dirichlet", "dirichlet"), T_bc=(0.0, 0.0, Ts, Ts),
-                strip=(x0, x0 + strip_width, Ts + dT_strip_ratio * Tc), G_wall=HEATED_WALL_G_WALL)
+                strip=(x0, x0 + strip_width, Ts + dT_strip_ratio * Tc),
+                G_wall=HEATED_WALL_G_WALL if G_wall is None else G_wall)
     return case, rho, T
 
 

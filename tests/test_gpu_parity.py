@@ -360,3 +360,15 @@ def test_poisoning_reaches_the_workspace(monkeypatch):
     sim.init(rho, T)
     assert int((sim.workspace == 255).sum()) > 0
     sim.close()
+
+
+@pytest.mark.parametrize("prec", F64, ids=F64_IDS)
+@pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
+def test_buoyancy_referenced_to_the_open_top_fp64(path, prec):
+    """Buoyancy 2, F_b = (rho - rho_bc[3]) g under the pressure top, on the ragged mixed grid."""
+    case, rho, T = workloads.mixed_small(TC, RV, RL)
+    case = dict(case, buoyancy=2)
+    gpu, f, _, _ = _gpu(case, rho, T, 150, prec=prec, path=path)
+    p, s = _oracle("mixed_small_b2", case, rho, T, 150)
+    _assert_within(_errors(gpu, p, s), 1e-10)
+    assert np.max(np.abs(f - s.f)) / np.max(np.abs(s.f)) < 1e-10

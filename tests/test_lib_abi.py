@@ -53,6 +53,9 @@ def test_check_params(lib):
         dict(t_bc=(1, 0, 0, 0)),  # Dirichlet needs T_bc > 0
         dict(strip=(3, 9, 0.1)),  # strip needs a Dirichlet y- edge
         dict(s_g=(1.0,) * 8 + (2.0,)), dict(cV=0.0), dict(lam=-1.0), dict(b=0.0),
+        dict(buoyancy=3), dict(buoyancy=-1),
+        dict(buoyancy=2),  # the reference density of buoyancy 2 is held on a pressure y+ edge
+        dict(buoyancy=2, flow_bc=(0, 0, lbpc.WALL, lbpc.WALL)),
     ]
     for kw in bad:
         p = lbpc.Params(**{**dict(nx=32, ny=16), **kw})
