@@ -264,8 +264,8 @@ def test_bench_workload_follows_the_d2_law():
 
 
 def test_heated_wall_with_open_top_runs_30000_steps():
-    """Configuration 3 as stated: 300 x 400 pool, heated strip, wall at y = 0, the top held at the vapour
-    density and T_s, g = 3e-5, FP32, 30 000 steps. With the buoyancy referenced to the top's density
+    """The heated-wall nucleation workload as specified: 300 x 400 pool, heated strip, wall at y = 0, the
+    top held at the vapour density and T_s, g = 3e-5, FP32, 30 000 steps. With the buoyancy referenced to the top's density
     (buoyancy 2, the workload's default under this top) the run stays physical, keeps its mass within
     1e-3 and holds a vapour region on the wall over the strip. With the domain mean as the reference it
     leaves the EOS range after about 1850 steps (both the oracle and the GPU)."""
