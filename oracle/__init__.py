@@ -18,6 +18,13 @@ model    The time step, whole-array passes in the order the paper states the mod
 Every function cites the passage it follows. Where the paper delegates a detail to a reference
 that is not reproduced in the paper (flow model, isotropic stencils, Zou-He, contact angle),
 the reading taken is stated in the docstring and marked READING.
+
+Pins (tests/test_oracle_*.py) check the oracle against what the paper and the mathematics fix. The
+no-slip wall is pinned by plane Poiseuille flow, by the mass of a liquid on a wettable wall, by the
+90-degree contact angle of a neutral wall, and by an open-top pool at hydrostatic rest. Parity
+unpinned: the fixed-density (pressure) edge's closure, the held-temperature rows and the heated strip
+(``flow_boundaries`` for a pressure edge, ``heat_boundaries``). The paper gives no data for them, so
+only GPU-oracle parity and the x-mirror invariant cover them.
 """
 
 from . import lattice, eos, model  # noqa: F401
