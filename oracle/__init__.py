@@ -21,10 +21,11 @@ the reading taken is stated in the docstring and marked READING.
 
 Pins (tests/test_oracle_*.py) check the oracle against what the paper and the mathematics fix. The
 no-slip wall is pinned by plane Poiseuille flow, by the mass of a liquid on a wettable wall, by the
-90-degree contact angle of a neutral wall, and by an open-top pool at hydrostatic rest. Parity
-unpinned: the fixed-density (pressure) edge's closure, the held-temperature rows and the heated strip
-(``flow_boundaries`` for a pressure edge, ``heat_boundaries``). The paper gives no data for them, so
-only GPU-oracle parity and the x-mirror invariant cover them.
+90-degree contact angle of a neutral wall, and by an open-top pool at hydrostatic rest. Held
+temperatures (``heat_boundaries``) are pinned by steady conduction between held rows. Parity
+unpinned: the fixed-density (pressure) edge's closure (``flow_boundaries`` for a pressure edge). The
+paper gives no data for it, so only GPU-oracle parity, the x-mirror invariant and the open-top rest
+state cover it.
 """
 
 from . import lattice, eos, model  # noqa: F401

@@ -92,3 +92,25 @@ def test_pool_under_an_open_top(mode):
         assert np.max(np.abs(uy)) < 1e-4 and abs(drift) < 1e-4, (np.max(np.abs(uy)), drift)
     else:
         assert np.mean(uy[-1]) > 2e-4 and drift < -1e-3, (np.mean(uy[-1]), drift)
+
+
+def test_steady_conduction_between_held_rows():
+    """Held temperatures (anti-bounce-back of the unknown g on the wall rows): between rows held at
+    T_lo and T_hi, a fluid at rest (the frozen-flow hook) reaches the linear conduction profile. Its
+    interior, three nodes or more from either wall, is linear to 1e-4 of dT, as the steady diffusion
+    equation requires. The heat flux is within 2 % of (T_hi - T_lo)/(ny - 1), and the wall rows sit within
+    0.5 % of dT of their held values. A sign error in the closure (no heat enters) or a wrong equilibrium
+    (a shifted wall temperature) fails it."""
+    nx, ny = 4, 21
+    T_lo, T_hi = 1.02 * TS, 0.98 * TS
+    dT = T_lo - T_hi
+    p = model.OracleParams(nx=nx, ny=ny, flow_bc=("periodic", "periodic", "wall", "wall"), frozen_flow=(0.0, 0.0),
+                           t_bc=("none", "none", "dirichlet", "dirichlet"), T_bc=(0, 0, T_lo, T_hi),
+                           lambda_mode="rho_cv_chi", chi=0.2)
+    s = model.run(p, model.init_state(p, np.full((ny, nx), RL), np.full((ny, nx), TS)), 3000)
+    T = model.fields(p, s)[3][:, 0]
+    y = np.arange(ny)
+    c = np.polyfit(y[3:-3], T[3:-3], 1)
+    assert np.max(np.abs(np.polyval(c, y[3:-3]) - T[3:-3])) < 1e-4 * dT
+    assert abs(c[0] / ((T_hi - T_lo) / (ny - 1)) - 1.0) < 0.02
+    assert abs(T[0] - T_lo) < 5e-3 * dT and abs(T[-1] - T_hi) < 5e-3 * dT
