@@ -22,10 +22,9 @@ the reading taken is stated in the docstring and marked READING.
 Pins (tests/test_oracle_*.py) check the oracle against what the paper and the mathematics fix. The
 no-slip wall is pinned by plane Poiseuille flow, by the mass of a liquid on a wettable wall, by the
 90-degree contact angle of a neutral wall, and by an open-top pool at hydrostatic rest. Held
-temperatures (``heat_boundaries``) are pinned by steady conduction between held rows. Parity
-unpinned: the fixed-density (pressure) edge's closure (``flow_boundaries`` for a pressure edge). The
-paper gives no data for it, so only GPU-oracle parity, the x-mirror invariant and the open-top rest
-state cover it.
+temperatures (``heat_boundaries``) are pinned by steady conduction between held rows. The
+fixed-density (pressure) edge is pinned by the values it prescribes (rho = rho_bc, u_x = 0 on its row)
+and by the hydrostatic rest of a pool under it.
 """
 
 from . import lattice, eos, model  # noqa: F401

@@ -86,10 +86,12 @@ def test_pool_under_an_open_top(mode):
     s = model.run(p, model.init_state(p, rho, T), 3000)
     m3000 = s.f.sum()
     s = model.run(p, s, 3000)
-    _, _, uy, _ = model.fields(p, s)
+    rho_f, ux, uy, _ = model.fields(p, s)
     drift = (s.f.sum() - m3000) / m3000
     if mode == 2:
         assert np.max(np.abs(uy)) < 1e-4 and abs(drift) < 1e-4, (np.max(np.abs(uy)), drift)
+        # the pressure edge holds what it prescribes: rho = rho_bc and u_x = 0 on the top row
+        assert np.max(np.abs(rho_f[-1] / RV - 1.0)) < 1e-13 and np.max(np.abs(ux[-1])) < 1e-15
     else:
         assert np.mean(uy[-1]) > 2e-4 and drift < -1e-3, (np.mean(uy[-1]), drift)
 
