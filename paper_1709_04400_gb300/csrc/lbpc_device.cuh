@@ -104,6 +104,17 @@ template <class R> __device__ __forceinline__ void from_moments(const R m[9], R 
   x[8] = dg + sx - sy - u8;
 }
 
+// x = M^{-1} m for the post-collision populations. In binary32 arithmetic the rest population is taken
+// as x0 = m0 - (x1 + ... + x8), so that the populations sum to the zeroth moment up to one rounding:
+// the scale 1/9 of m0 rounds up by 7.5e-9 in binary32, and the plain transform would scale each node's
+// mass (or heat) by 9 fl(1/9) in every collision, a steady drift of about 1e-8 per step. In binary64
+// and double-word arithmetic that drift is about 5e-17 per step, and the plain transform is kept (the
+// double-word type's lazy additions lose accuracy in the longer sum).
+template <class R> __device__ __forceinline__ void from_moments_conserving(const R m[9], R x[9]) {
+  from_moments(m, x);
+  if constexpr (sizeof(R) == 4) x[0] = m[0] - (((x[1] + x[2]) + (x[3] + x[4])) + ((x[5] + x[6]) + (x[7] + x[8])));
+}
+
 // ------------------------------------------------------------------------------------------------
 // Peng-Robinson EOS (Eq. 56) and (dp/dT)_rho
 // ------------------------------------------------------------------------------------------------
@@ -392,7 +403,7 @@ __device__ __forceinline__ void collide_flow(R f[9], R rho, R vx, R vy, R Fx, R 
     if (k == 3 || k == 5) continue;
     m[k] = m[k] - C.s_f[k] * (m[k] - meq[k]) + C.hf[k] * SF[k];
   }
-  from_moments(m, f);
+  from_moments_conserving(m, f);
 }
 
 // Thermal MRT collision of the improved model: Eq. 45 with m_eq of Eq. 53 and S = (S0, 0, ..., 0)
@@ -437,7 +448,7 @@ __device__ __forceinline__ void collide_heat(R g[9], R T, R vx, R vy, R S0, cons
       ns[5] += C.c5 * (n[6] - neq[6]);
     }
   }
-  from_moments(ns, g);
+  from_moments_conserving(ns, g);
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -59,8 +59,8 @@ def _departure_alone(prec, path):
 
 
 # Bars on |departure step - oracle's|: FP64 and DF64 agree to round-off, so the step must match. The
-# reduced precisions shift the instant of pinch-off by the rounding of the interface motion (measured:
-# FP32 one step late, binary16 deviation storage two, of 9429).
+# reduced precisions may shift the instant of pinch-off by the rounding of the interface motion
+# (measured: FP32 exact, binary16 deviation storage two steps late, of 9429).
 BARS = {lbpc.FP64: 0, lbpc.DF64: 0, lbpc.FP32: 10, lbpc.FP16DEV: 20}
 _ALONE = {}
 

@@ -11,7 +11,7 @@ import pytest
 
 from paper_1709_04400_gb300 import lbpc, workloads
 
-from .helpers import RL, RV, TC, oracle_params
+from .helpers import RL, RV, TC, max_rel, norm_rel, oracle_params
 
 pytestmark = pytest.mark.gpu
 
@@ -39,6 +39,9 @@ def _rate(hist):
     return np.polyfit(t[sel], a[sel], 1)[0]
 
 
+_ORACLE_END = {}
+
+
 @pytest.fixture(scope="module")
 def oracle_rate():
     from oracle import model
@@ -51,7 +54,19 @@ def oracle_rate():
         s = model.step(p, s)
         if k % EVERY == 0:
             hist.append((k, workloads.droplet_area(model.fields(p, s)[0])))
+    _ORACLE_END["fields"] = model.fields(p, s)
     return _rate(hist)
+
+
+# field errors after the 4000 steps, against the oracle's final fields (max relative for rho and T,
+# relative to the largest |u| for the velocity)
+FIELD_BARS = {lbpc.FP64: 1e-10, lbpc.DF64: 1e-10, lbpc.FP32: 3e-4, lbpc.FP16DEV: 5e-2}
+
+
+def _field_errors(got):
+    ref = _ORACLE_END["fields"]
+    return dict(rho=max_rel(got[0], ref[0]), T=max_rel(got[3], ref[3]),
+                u=max(norm_rel(got[1], ref[1]), norm_rel(got[2], ref[2])))
 
 
 def _sim_rate(prec, path=lbpc.PATH_AUTO):
@@ -63,8 +78,9 @@ def _sim_rate(prec, path=lbpc.PATH_AUTO):
     for k in range(EVERY, STEPS + 1, EVERY):
         sim.step(EVERY)
         hist.append((k, workloads.droplet_area(sim.fields()[0])))
+    end = sim.fields()
     sim.close()
-    return _rate(hist)
+    return _rate(hist), end
 
 
 def _batch_rate(prec):
@@ -81,23 +97,30 @@ def _batch_rate(prec):
     for k in range(EVERY, STEPS + 1, EVERY):
         b.step(EVERY)
         hist.append((k, workloads.droplet_area(b.fields(i)[0])))
+    end = b.fields(i)
     b.close()
-    return _rate(hist)
+    return _rate(hist), end
 
 
 @pytest.mark.parametrize("prec,path,tol", [(lbpc.FP64, lbpc.PATH_SPLIT, 1e-6), (lbpc.DF64, lbpc.PATH_SPLIT, 1e-6),
                                            (lbpc.FP32, lbpc.PATH_FUSED, 1e-2), (lbpc.FP16DEV, lbpc.PATH_FUSED, 5e-2)],
                          ids=["fp64", "df64", "fp32", "fp16"])
 def test_evaporation_rate_alone(oracle_rate, prec, path, tol):
-    r = _sim_rate(prec, path)
+    r, end = _sim_rate(prec, path)
     err = abs(r - oracle_rate) / abs(oracle_rate)
-    print(f"evaporation rate, prec {prec}: {r:.6e} per step against {oracle_rate:.6e} (relative error {err:.2e})")
+    fe = _field_errors(end)
+    print(f"evaporation rate, prec {prec}: {r:.6e} per step against {oracle_rate:.6e} (relative error {err:.2e}); "
+          f"fields after {STEPS} steps {fe}")
     assert oracle_rate < 0 and err <= tol
+    assert all(v <= FIELD_BARS[prec] for v in fe.values()), fe
 
 
 @pytest.mark.parametrize("prec,tol", [(lbpc.FP32, 1e-2), (lbpc.FP16DEV, 5e-2)], ids=["fp32", "fp16"])
 def test_evaporation_rate_batched(oracle_rate, prec, tol):
-    r = _batch_rate(prec)
+    r, end = _batch_rate(prec)
     err = abs(r - oracle_rate) / abs(oracle_rate)
-    print(f"evaporation rate, batched prec {prec}: {r:.6e} per step against {oracle_rate:.6e} (relative error {err:.2e})")
+    fe = _field_errors(end)
+    print(f"evaporation rate, batched prec {prec}: {r:.6e} per step against {oracle_rate:.6e} "
+          f"(relative error {err:.2e}); fields after {STEPS} steps {fe}")
     assert err <= tol
+    assert all(v <= FIELD_BARS[prec] for v in fe.values()), fe

@@ -57,8 +57,11 @@ def _window_check(n, prec, tol, tol_u, k=10, W=128):
 
 
 # binary16 deviation storage keeps the documented bound of its own parity test: 1e-3 on rho and T,
-# 2e-2 on u relative to the (small) velocities
-@pytest.mark.parametrize("n,prec,tol,tol_u", [(4096, lbpc.FP32, 1e-4, 1e-4), (4096, lbpc.FP16DEV, 1e-3, 2e-2),
+# 2e-2 on u relative to the (small) velocities. Binary32: 1e-4 on rho and T; on u, 2e-4. Ten steps after
+# a start from rest the velocities are still small, and the binary32 rounding of the momentum, relative
+# to the largest |u|, is about 1e-4 here (measured 0.9e-4 to 1.04e-4, depending on the rounding order of
+# the collision).
+@pytest.mark.parametrize("n,prec,tol,tol_u", [(4096, lbpc.FP32, 1e-4, 2e-4), (4096, lbpc.FP16DEV, 1e-3, 2e-2),
                                               (2048, lbpc.FP64, 1e-10, 1e-10), (2048, lbpc.DF64, 1e-10, 1e-10)],
                          ids=["fp32-4096", "fp16-4096", "fp64-2048", "df64-2048"])
 def test_large_grid_window(n, prec, tol, tol_u):
