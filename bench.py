@@ -242,7 +242,7 @@ def _dtypes():
 # kernel must refresh its entry or remove it (the line then reports null).
 MEASURED_TRAFFIC = {
     ("k_collide", "droplet_evaporation_256_dT0.1Tc", "fp64"): 14_743_040,
-    ("k_fused", "droplet_evaporation_4096_dT0.1Tc", "fp32"): 2_508_875_264,
+    ("k_fused", "droplet_evaporation_4096_dT0.1Tc", "fp32"): 2_508_742_144,
     ("k_collide", "droplet_evaporation_2048_dT0.1Tc", "df64"): 1_639_130_112,
     # batched step, 32x8 tiles (variant 0): 147.9 B/node captured on 96 instances (9.8 M nodes; 145 B/node on
     # 48), scaled by nodes to the 256 instances (27.1 M nodes)
