@@ -46,7 +46,8 @@ def parse(argv=None):
     ap.add_argument("--variant", type=int, default=-1,
                     help="batched workload: step-kernel variant 0-5 instead of the autotuner's choice")
     ap.add_argument("--ctas", type=int, default=16, help="batched workload with --variant: CTAs per SM")
-    ap.add_argument("--n", type=int, default=0, help="grid side (0 = the workload's own size)")
+    ap.add_argument("--n", type=int, default=0,
+                    help="grid side (0 = the workload's own size); batched workload: every instance of this side")
     ap.add_argument("--dT", type=float, default=0.1, help="superheat dT / T_c of the evaporation case")
     ap.add_argument("--prec", default="", choices=["", "fp64", "df64", "fp32", "fp16"])
     ap.add_argument("--path", default="auto", choices=["auto", "split", "fused"])
@@ -461,7 +462,13 @@ def run_batch(args):
     rv, rl, _ = lbpc.coexistence(p0, 0.86 * Tc)
     prec_name = args.prec or "fp32"
     prec = {"fp64": lbpc.FP64, "fp32": lbpc.FP32, "fp16": lbpc.FP16DEV}[prec_name]
-    insts = workloads.batched_evaporation(Tc, rv, rl, count=args.instances)
+    if args.n:  # every instance the evaporation case of side n (R = 0.2 n)
+        one = workloads.droplet_evaporation(Tc, rv, rl, n=args.n, radius=0.2 * args.n, dT_ratio=args.dT)
+        insts = [one] * args.instances
+        wname = f"evaporation_{args.n}_x{args.instances}"
+    else:
+        insts = workloads.batched_evaporation(Tc, rv, rl, count=args.instances)
+        wname = f"batched_evaporation_{len(insts)}"
     params = [lbpc.params_from_case(c, prec) for c, _, _ in insts]
     nodes = sum(p.nx * p.ny for p in params)
     arena = sum(lbpc.Batch.instance_bytes(p) for p in params) + (256 << 20)
@@ -520,7 +527,7 @@ def run_batch(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": batch_s * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == lbpc.FP64 else "f32", "data": "synthetic",
-        "config": {"workload": f"batched_evaporation_{len(insts)}", "instances": len(insts), "nodes": nodes,
+        "config": {"workload": wname, "instances": len(insts), "nodes": nodes,
                    "storage": prec_name, "tile": [cfg["tile_x"], cfg["tile_y"]], "ctas_per_sm": cfg["ctas_per_sm"],
                    "graph_chunk": cfg["graph_chunk"], "autotune": tuned,
                    "l2": "working set of %.1f GB exceeds L2" % (nodes * fused_bytes_per_node(pb) / 1e9)},
@@ -529,8 +536,7 @@ def run_batch(args):
         "batched_over_plain": value / plain,
         "roofline": {"bound": "hbm", "kernel": "k_batch_step", "achieved": achieved, "peak": peak_bw, "unit": "GB/s",
                      "frac": achieved / peak_bw,
-                     "traffic": MEASURED_TRAFFIC.get(("k_batch_step", f"batched_evaporation_{args.instances}",
-                                                      prec_name, tuned.get("variant", -1))),
+                     "traffic": MEASURED_TRAFFIC.get(("k_batch_step", wname, prec_name, tuned.get("variant", -1))),
                      "bytes_per_node": fused_bytes_per_node(pb),
                      "frac_of_nominal": achieved / NOMINAL_HBM_GBS},
         "gpu_launches": 2 * args.steps, "clocks": clk.summary(),
