@@ -88,7 +88,10 @@ Layout layout_of(const lbpc_params* p) {
   }
   L.phi = off; off += align256((size_t)L.N * L.real);
   L.planes = off; off += (size_t)lbpc::split_nplanes() * align256((size_t)L.N * L.real);
-  L.partials = off; off += align256(2 * (size_t)L.nblocks * sizeof(double));
+  // per-block partials of the split step, or per-tile partials of the fused step (more on narrow domains)
+  const size_t npartials = 2 * (size_t)L.nblocks > lbpc::fused_max_tiles(p->nx, p->ny)
+                               ? 2 * (size_t)L.nblocks : lbpc::fused_max_tiles(p->nx, p->ny);
+  L.partials = off; off += align256(npartials * sizeof(double));
   L.scalars = off; off += align256(8 * sizeof(double));
   L.status = off; off += align256(8 * sizeof(long long));
   L.total = off;

@@ -94,9 +94,6 @@ struct HostInst {
 size_t store_bytes(int prec) { return prec == LBPC_FP64 ? 8 : (prec == LBPC_FP32 ? 4 : 2); }
 size_t real_bytes(int prec) { return prec == LBPC_FP64 ? 8 : 4; }
 
-// Largest number of tiles an instance can have over the tile shapes (the 32 x 8 shape).
-size_t max_tiles(const lbpc_params* p) { return (size_t)((p->nx + 31) / 32) * ((p->ny + 7) / 8); }
-
 // Lay out one instance inside a block starting at 0; returns the block size.
 size_t layout_instance(const lbpc_params* p, HostInst* h) {
   const long long N = (long long)p->nx * p->ny;
@@ -117,7 +114,7 @@ size_t layout_instance(const lbpc_params* p, HostInst* h) {
     h->wall[k] = off; off += a256((size_t)lbpc::wall_doubles(p->nx) * sizeof(double));
   }
   h->phi = off; off += a256((size_t)N * rb);
-  h->npartials = std::max(max_tiles(p), 2 * (size_t)((N + lbpc::split_block() - 1) / lbpc::split_block()));
+  h->npartials = std::max(lbpc::fused_max_tiles(p->nx, p->ny), 2 * (size_t)((N + lbpc::split_block() - 1) / lbpc::split_block()));
   h->partials = off; off += a256(h->npartials * sizeof(double));
   h->scalars = off; off += a256(8 * sizeof(double));
   return off;

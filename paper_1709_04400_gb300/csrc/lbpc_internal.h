@@ -36,6 +36,11 @@ struct alignas(64) TmaMaps {
 };
 
 
+// Most tiles a fused or batched step launches over an nx x ny domain (the 32 x 8 tile, the smallest
+// shape). A step with the domain-mean buoyancy writes one partial sum per tile, so the partials array
+// holds at least this many; on narrow domains (nx < 4) it exceeds the 2 * ceil(N / 64) of the split step.
+inline size_t fused_max_tiles(int nx, int ny) { return (size_t)((nx + 31) / 32) * (size_t)((ny + 7) / 8); }
+
 // Fused-step tile configuration a new context starts with: 32 x 8 tiles, one node per thread (the
 // fastest measured on GB300 at 2048^2 - 4096^2 in FP32 and FP16).
 constexpr int kDefaultFusedTile = 1;
@@ -49,7 +54,7 @@ struct SplitBuffers {
   double* wall[2] = {nullptr, nullptr};  // wall-row forces stored with f (A/B, wall_doubles(nx) each); null if y is periodic
   void* phi_prev;    // phi(t - dt), arithmetic type
   void* planes[16];  // scratch planes of the split kernels, arithmetic type
-  double* partials;  // 2 * nblocks per-block partial sums
+  double* partials;  // per-block (split) or per-tile (fused) partial sums: max(2 * nblocks, fused_max_tiles)
   double* scalars;   // [0] rho_ave, [1] mass, [2] heat
   long long* status; // [0] flag, [1] step, [2] x, [3] y, [4] code
   const TmaMaps* tma[2] = {nullptr, nullptr};  // tensor maps of buffer A / B for the TMA-staged fused step

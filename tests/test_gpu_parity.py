@@ -201,6 +201,19 @@ def test_smallest_grid_and_zero_steps():
     _assert_within(_errors(gpu, p, s), 1e-10)
 
 
+@pytest.mark.parametrize("nx", [2, 3])
+@pytest.mark.parametrize("prec,tol", [(lbpc.FP64, 1e-10), (lbpc.FP32, 1e-4)], ids=["fp64", "fp32"])
+def test_narrow_tall_channel_fused(prec, tol, nx):
+    """nx = 2 or 3, ny = 2048 with the domain-mean buoyancy on the fused path: 256 tiles of 32 x 8 for
+    only 4096-6144 nodes, more tiles than 64-node blocks. Each tile's partial sum of rho must land in
+    its own slot, and the mean they give must be the oracle's."""
+    case, rho, T = workloads.mixed_small(TC, RV, RL, nx=nx, ny=2048)
+    steps = 20
+    p, s = _oracle(f"narrow_{nx}", case, rho, T, steps)
+    gpu, _, _, _ = _gpu(case, rho, T, steps, prec=prec, path=lbpc.PATH_FUSED)
+    _assert_within(_errors(gpu, p, s), tol)
+
+
 def test_device_pointers_and_async_steps():
     import torch
 
