@@ -261,6 +261,9 @@ class Simulation:
         import torch
 
         if isinstance(rho, torch.Tensor):
+            for name, x in zip(("rho", "T", "ux", "uy"), (rho, T, ux, uy)):
+                if x is not None and x.numel() != self.nx * self.ny:  # the kernels read nx * ny values
+                    raise ValueError(f"{name} has {x.numel()} values, the grid {self.ny} x {self.nx}")
             args = [x if x is None else x.to(device=self.device, dtype=torch.float64).contiguous() for x in (rho, T, ux, uy)]
             ptrs = [ctypes.c_void_p(0) if x is None else ctypes.c_void_p(x.data_ptr()) for x in args]
             self._keep = args
@@ -310,6 +313,10 @@ class Simulation:
     def sums_async(self, out):
         """Enqueue the domain sums and a copy of (mass, heat) into out, a 2-element float64 CUDA tensor
         or pinned host tensor, without waiting (lbpc_sums_async)."""
+        import torch
+
+        if out.dtype != torch.float64 or out.numel() < 2 or not out.is_contiguous():
+            raise ValueError("sums_async needs a contiguous float64 tensor of at least 2 elements")
         self._raise(self.lib.lbpc_sums_async(self.ctx, ctypes.c_void_p(out.data_ptr()), int(out.is_cuda)),
                     "lbpc_sums_async")
 

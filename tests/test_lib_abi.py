@@ -96,3 +96,22 @@ def test_simulation_refuses_without_gpu():
         pytest.skip("a GPU is present")
     with pytest.raises(RuntimeError):
         lbpc.Simulation(lbpc.Params(nx=8, ny=8))
+
+
+def test_binding_refuses_device_buffers_of_the_wrong_size():
+    """The binding checks the sizes of tensors whose pointers it passes to the kernels (a short tensor
+    would be read or written past its end on the device). The checks run before any library call, so a
+    context-less object stands in for a Simulation here."""
+    import torch
+
+    sim = object.__new__(lbpc.Simulation)
+    sim.nx, sim.ny = 8, 6
+    with pytest.raises(ValueError):
+        sim.init(torch.zeros(47, dtype=torch.float64), torch.zeros(48, dtype=torch.float64))
+    with pytest.raises(ValueError):
+        sim.init(torch.zeros(48, dtype=torch.float64), torch.zeros(48, dtype=torch.float64),
+                 ux=torch.zeros(40, dtype=torch.float64))
+    for bad in (torch.zeros(1, dtype=torch.float64), torch.zeros(2, dtype=torch.float32),
+                torch.zeros(4, dtype=torch.float64)[::2]):
+        with pytest.raises(ValueError):
+            sim.sums_async(bad)
