@@ -115,3 +115,42 @@ def test_binding_refuses_device_buffers_of_the_wrong_size():
                 torch.zeros(4, dtype=torch.float64)[::2]):
         with pytest.raises(ValueError):
             sim.sums_async(bad)
+
+
+def _every_workload():
+    from paper_1709_04400_gb300 import serve, workloads
+
+    yield workloads.droplet_periodic(TC, RV, RL)
+    yield workloads.droplet_evaporation(TC, RV, RL)
+    yield workloads.droplet_evaporation(TC, RV, RL, n=4096, radius=0.2 * 4096)
+    for top in ("pressure", "wall"):
+        yield workloads.heated_wall(TC, RV, RL, top=top)
+    yield workloads.bubble_departure(TC, RV, RL)
+    for model in ("improved", "compromised", "gong_cheng"):
+        yield workloads.droplet_on_surface(TC, RV, RL, model=model, wall_T_ratio=0.875)
+        yield workloads.paper_d2_law(TC, RV, RL, model=model)
+    yield workloads.droplet_on_surface(TC, RV, RL, lambda_mode="const")
+    for nx, ny in ((37, 29), (2, 3), (2, 2048), (3, 2048)):
+        yield workloads.mixed_small(TC, RV, RL, nx=nx, ny=ny)
+    yield from workloads.batched_evaporation(TC, RV, RL, count=8)
+    for req in serve.poisson_stream(40, 1.0, seed=11):
+        yield serve.make_case(req, TC, RV, RL)
+
+
+def test_every_workload_is_accepted_by_library_and_oracle(lib):
+    """Each seeded workload (the bench's, the tests', the paper cases', the service's requests) passes
+    the library's parameter check in every precision and the oracle's, and its initial fields have the
+    grid's shape and physical values (0 < rho < 1/b, T > 0)."""
+    from .helpers import oracle_params
+
+    b = 2.0 / 21.0
+    count = 0
+    for case, rho, T in _every_workload():
+        assert rho.shape == T.shape == (case["ny"], case["nx"]), case["name"]
+        assert np.all(rho > 0) and np.all(rho < 1.0 / b) and np.all(T > 0), case["name"]
+        oracle_params(case).check()
+        for prec in (lbpc.FP64, lbpc.DF64, lbpc.FP32, lbpc.FP16DEV):
+            s, msg = lbpc.check_params(lbpc.params_from_case(case, prec))
+            assert s == lbpc.LBPC_OK, (case["name"], prec, msg)
+        count += 1
+    assert count > 60
