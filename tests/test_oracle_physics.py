@@ -1,5 +1,6 @@
-"""Physics pins of the oracle (the five references the coupled method must reproduce):
-mass conservation (test_oracle_invariants), the analytic chi q^2 decay of a temperature mode,
+"""Physics pins of the oracle (the references the coupled method must reproduce):
+mass conservation (test_oracle_invariants), the analytic chi q^2 decay of a temperature mode, the
+adiabatic heating of a compression wave,
 the Chapman-Enskog prediction for advected heat (improved vs compromised model), the Laplace law,
 EOS-consistent coexistence of a flat interface and the D^2 law of droplet evaporation."""
 
@@ -43,6 +44,40 @@ def test_chi_q2_decay(rho0):
     err32, err64 = abs(r32 / e32 - 1), abs(r64 / e64 - 1)
     assert err64 < 0.006
     assert 3.5 < err32 / err64 < 4.5
+
+
+def _compression_slope(rho0, N, steps=40, amp=1e-3, lam=0.01):
+    """Slope of T - T0 against rho - rho0, over all nodes, after `steps` steps of the acoustic wave
+    started by u_x = amp sin(q x) in a uniform fluid at (rho0, T_s), and the slope the energy
+    equation predicts for it."""
+    q = 2 * np.pi / N
+    p = model.OracleParams(nx=N, ny=4, lam=lam)
+    x = np.arange(N)[None, :] * np.ones((4, 1))
+    s = model.init_state(p, np.full((4, N), rho0), np.full((4, N), TS), ux=amp * np.sin(q * x),
+                         uy=np.zeros((4, N)))
+    rho, _, _, T = model.fields(p, model.run(p, s, steps))
+    dr, dT = rho - rho0, T - TS
+    # (dp/dT)_rho by a central difference of the Peng-Robinson pressure (Eq. 56), not eos.dp_dT
+    h = 1e-6 * TS
+    dpdT = (eos.pressure(rho0, TS + h, A, B, R, OM) - eos.pressure(rho0, TS - h, A, B, R, OM)) / (2 * h)
+    return (dT * dr).sum() / (dr * dr).sum(), TS * dpdT / (rho0 * rho0 * 5.0)
+
+
+@pytest.mark.parametrize("rho0", [RV, RL], ids=["vapour", "liquid"])
+def test_compression_heats_along_the_adiabat(rho0):
+    """The pressure-work term of the source. The energy equation the model recovers (Eq. 5),
+    rho c_V DT/Dt = div(lambda grad T) - T (dp/dT)_rho div v, with continuity D rho/Dt = -rho div v,
+    makes a small, fast compression follow dT/d rho = T (dp/dT)_rho / (rho^2 c_V) when conduction is
+    negligible. An acoustic wave in a uniform vapour or liquid must therefore carry temperature and
+    density perturbations in that ratio at every node. Dropping T[1 - (dp/dT)_rho/(rho c_V)] div v from
+    phi, flipping its sign or dividing by c_V instead of rho c_V changes the ratio by 60 % to 550 %.
+    The error falls at second order in the wavelength: vapour 0.44 % at 128 nodes and 0.11 % at 256,
+    liquid 0.09 % and 0.02 %."""
+    s128, want = _compression_slope(rho0, 128)
+    s256, _ = _compression_slope(rho0, 256)
+    err128, err256 = abs(s128 / want - 1), abs(s256 / want - 1)
+    assert err256 < 0.005
+    assert 3.0 < err128 / err256 < 5.0
 
 
 def _advect(mdl, v0=0.1, nsteps=300):
