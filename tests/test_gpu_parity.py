@@ -139,7 +139,7 @@ def test_wall_top_and_pressure_bottom_fp64(path, prec):
 @pytest.mark.parametrize("prec", F64, ids=F64_IDS)
 @pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
 def test_droplet_periodic_128_fp64_1000_steps(path, prec):
-    """The 128 x 128 periodic droplet: 1000 steps, 1e-10 on rho, u, T (spec parity bar)."""
+    """The 128 x 128 periodic droplet: 1000 steps, 1e-10 on rho, u, T (the FP64 parity bar)."""
     case, rho, T = workloads.droplet_periodic(TC, RV, RL)
     gpu, _, _, (mass, heat) = _gpu(case, rho, T, 1000, prec=prec, path=path)
     p, s = _oracle("droplet_periodic_128", case, rho, T, 1000)

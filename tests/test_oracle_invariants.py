@@ -25,7 +25,7 @@ def _params(nx, ny, **kw):
 
 
 def test_mass_conservation_periodic_1000_steps():
-    """North-star reference 1: exact mass conservation on a periodic domain."""
+    """Exact mass conservation on a periodic domain."""
     p = _params(32, 32, lambda_mode="rho_cv_chi", chi=0.06)
     rho, T, _ = inputs.droplet_periodic(inputs.SEED_BASE, 32, 32, 8, 4, RL, RV, TC)
     s = model.init_state(p, rho, T)

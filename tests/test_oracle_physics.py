@@ -140,8 +140,8 @@ def test_advection_error_term_removed():
 
 @pytest.mark.slow
 def test_laplace_law():
-    """North-star reference 3: static droplets, isothermal; p_in - p_out is linear in 1/R with a
-    vanishing intercept."""
+    """Laplace law: static droplets, isothermal; p_in - p_out is linear in 1/R with a vanishing
+    intercept."""
     N = 64
     res = []
     for Rd in (10, 13, 16):
@@ -160,7 +160,7 @@ def test_laplace_law():
 
 @pytest.mark.slow
 def test_flat_interface_coexistence():
-    """North-star reference 4: a periodic liquid slab reaches plateau densities close to the Maxwell
+    """Coexistence: a periodic liquid slab reaches plateau densities close to the Maxwell
     coexistence values of Eq. 56 at T_sat = 0.86 T_c (the sigma term tunes this; pseudopotential
     models are not exactly thermodynamically consistent)."""
     p = model.OracleParams(nx=4, ny=128, frozen_thermal=True)
@@ -174,7 +174,7 @@ def test_flat_interface_coexistence():
 
 @pytest.mark.slow
 def test_d2_law():
-    """North-star reference 5 (Sec. IV A, Fig. 2): a droplet at T_sat in superheated surroundings
+    """D^2 law (Sec. IV A, Fig. 2): a droplet at T_sat in superheated surroundings
     evaporates with (D/D0)^2 linear in time after the initial transient."""
     N, Rd, dT = 64, 14.0, 0.3 * TC
     p = model.OracleParams(nx=N, ny=N, t_bc=("dirichlet",) * 4, T_bc=(TS + dT,) * 4)
