@@ -20,7 +20,10 @@ that is not reproduced in the paper (flow model, isotropic stencils, Zou-He, con
 the reading taken is stated in the docstring and marked READING.
 
 Pins (tests/test_oracle_*.py) check the oracle against what the paper and the mathematics fix. The
-no-slip wall is pinned by plane Poiseuille flow, by the mass of a liquid on a wettable wall, by the
+source phi is pinned term by term: conduction by the chi q^2 decay of a temperature mode and by the
+constant heat content of a fluid at rest under a variable conductivity; the pressure work, and the
+second-order time discretisation of Eq. 46, by the adiabatic temperature-density ratio of an acoustic
+wave. Eqs. 54-55 are pinned by the spreading of heat advected by a uniform flow. The no-slip wall is pinned by plane Poiseuille flow, by the mass of a liquid on a wettable wall, by the
 90-degree contact angle of a neutral wall, and by an open-top pool at hydrostatic rest. Held
 temperatures (``heat_boundaries``) are pinned by steady conduction between held rows. The
 fixed-density (pressure) edge is pinned by the values it prescribes (rho = rho_bc, u_x = 0 on its row)
