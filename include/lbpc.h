@@ -168,7 +168,10 @@ const char* lbpc_kernel_name(const lbpc_ctx* c, int32_t k);
  * scratch planes (each EOS evaluated once per node; the faster choice when FP64 arithmetic bounds
  * the step). LBPC_PATH_FUSED: one kernel per step over shared-memory tiles (populations read once
  * and written once; the faster choice when HBM bounds the step). LBPC_PATH_AUTO (default): split
- * for LBPC_FP64 and LBPC_DF64, fused for LBPC_FP32 and LBPC_FP16DEV. Both compute the same step. */
+ * for LBPC_FP64 and LBPC_DF64, fused for LBPC_FP32 and LBPC_FP16DEV. Both compute the same step.
+ * The fused step launches one row of CTAs per 8 grid rows, and a launch has at most 65,535 rows of
+ * CTAs: for ny > 524,280, LBPC_PATH_AUTO takes the split step and LBPC_PATH_FUSED returns
+ * LBPC_EINVAL. */
 typedef enum { LBPC_PATH_AUTO = 0, LBPC_PATH_SPLIT = 1, LBPC_PATH_FUSED = 2 } lbpc_path;
 lbpc_status lbpc_set_path(lbpc_ctx* c, int32_t path);
 

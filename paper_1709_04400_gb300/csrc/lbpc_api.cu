@@ -411,9 +411,13 @@ LBPC_API lbpc_status lbpc_init(lbpc_ctx* c, const double* rho, const double* T, 
   return LBPC_OK;
 }
 
+// The fused step's grid has one row of CTAs per tile row; the smallest tile is 8 rows high and a
+// launch holds at most 65,535 rows of CTAs.
+static bool fused_grid_fits(const lbpc_params& p) { return (p.ny + 7) / 8 <= 65535; }
+
 static bool use_fused(const lbpc_ctx* c) {
   return c->path == LBPC_PATH_FUSED ||
-         (c->path == LBPC_PATH_AUTO && c->p.prec != LBPC_FP64 && c->p.prec != LBPC_DF64);
+         (c->path == LBPC_PATH_AUTO && c->p.prec != LBPC_FP64 && c->p.prec != LBPC_DF64 && fused_grid_fits(c->p));
 }
 
 static cudaError_t launch_step(lbpc_ctx* c, cudaEvent_t* ev) {
@@ -432,6 +436,7 @@ static const char* step_kernel_name(const lbpc_ctx* c, int k) {
 
 LBPC_API lbpc_status lbpc_set_path(lbpc_ctx* c, int32_t path) {
   if (!c || path < LBPC_PATH_AUTO || path > LBPC_PATH_FUSED) return LBPC_EINVAL;
+  if (path == LBPC_PATH_FUSED && !fused_grid_fits(c->p)) return LBPC_EINVAL;
   c->path = path;
   return LBPC_OK;
 }

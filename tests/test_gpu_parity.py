@@ -214,6 +214,32 @@ def test_narrow_tall_channel_fused(prec, tol, nx):
     _assert_within(_errors(gpu, p, s), tol)
 
 
+def test_tall_channel_takes_the_split_step():
+    """ny = 524,296 needs 65,537 rows of 32 x 8 tiles, more rows of CTAs than a launch holds: FP32 on
+    the default path takes the split step (same bits as asking for it) and agrees with the oracle; asking
+    for the fused step is refused and leaves the context usable."""
+    case, rho, T = workloads.mixed_small(TC, RV, RL, nx=2, ny=524_296)
+    steps = 3
+    out = []
+    for path in (lbpc.PATH_AUTO, lbpc.PATH_SPLIT):
+        sim = lbpc.Simulation(lbpc.params_from_case(case, lbpc.FP32))
+        if path == lbpc.PATH_AUTO:
+            with pytest.raises(lbpc.LbpcError):
+                sim.set_path(lbpc.PATH_FUSED)
+        sim.set_path(path)
+        sim.init(rho, T)
+        sim.step(steps)
+        out.append(sim.fields())
+        sim.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+    p, s = run_oracle(case, rho, T, steps)
+    err = _errors(out[0], p, s)
+    # FP32 bar on rho and T; u is relative to the largest |u|, still small three steps after a start
+    # from rest, where the binary32 rounding of the momentum reaches about 1.2e-4 of it
+    assert err["rho"] <= 1e-4 and err["T"] <= 1e-4 and err["ux"] <= 2e-4 and err["uy"] <= 2e-4, err
+
+
 def test_device_pointers_and_async_steps():
     import torch
 
