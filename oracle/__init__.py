@@ -20,6 +20,10 @@ that is not reproduced in the paper (flow model, isotropic stencils, Zou-He, con
 the reading taken is stated in the docstring and marked READING.
 
 Pins (tests/test_oracle_*.py) check the oracle against what the paper and the mathematics fix. The
+flow collision with forcing reduces, with every MRT rate equal and sigma = 0, to BGK with Guo's
+forcing term, a textbook closed form checked node by node with v and F in both directions (every row
+of S_F, the velocity-dependent ones included); the sigma term is checked to change only the two energy
+moments, by the amounts its formula fixes, for an interaction force built in closed form. The
 source phi is pinned term by term: conduction by the chi q^2 decay of a temperature mode and by the
 constant heat content of a fluid at rest under a variable conductivity; the pressure work, and the
 second-order time discretisation of Eq. 46, by the adiabatic temperature-density ratio of an acoustic
