@@ -205,7 +205,10 @@ lbpc_status lbpc_sums_async(lbpc_ctx* c, double* out, int on_device);
  * service that moves or pre-empts simulations.
  *
  * A checkpoint is the context's whole state in raw form:
- *   - a 512-byte header: magic, version, the lbpc_params, the step counter and the lagged rho_ave;
+ *   - a 512-byte header holding, in this order and without gaps: the 8 bytes "LBPCCKP1", the format
+ *     version (uint32, 2), the header size (uint32, 512), the lbpc_params, the step counter (int64),
+ *     the lagged rho_ave (double) and the byte sizes of the four sections below (uint64 each:
+ *     populations of one set, reference planes of one set, phi, wall forces); the rest is zero;
  *   - the current post-collision populations f and g in the storage type, plus the FP16 reference
  *     planes for LBPC_FP16DEV;
  *   - phi of the previous step, in the arithmetic type;
@@ -310,6 +313,20 @@ const char* lbpc_batch_last_error(const lbpc_batch* b);
 void lbpc_batch_destroy(lbpc_batch* b);
 
 /* ------------------------------------------------------------------------------------------------
+ * FMA throughput of the current device: the measured denominator of the roofline of ALU-bound kernels
+ * (the binary64 step is bound by the FP64 pipe on this GPU). The paper has no counterpart; this is a
+ * measurement aid, not part of the method.
+ *
+ *   prec        LBPC_FP64 (binary64 FMA) or LBPC_FP32 (binary32 FMA)
+ *   stream      cudaStream_t the probe runs on; the call synchronises it
+ *   flop_per_s  receives 2 x the FMAs per second of one timed launch (after one warm-up launch) of a
+ *               probe kernel whose threads each run 8 independent FMA chains, on every SM with as many
+ *               CTAs as can be resident (about 30 ms in binary64, 20 ms in binary32)
+ * Allocates no device memory. Returns LBPC_EINVAL for another prec or a null pointer, LBPC_ECUDA if a
+ * launch fails. */
+lbpc_status lbpc_fma_rate(int32_t prec, void* stream, double* flop_per_s);
+
+/* ------------------------------------------------------------------------------------------------
  * One time step without any device allocation.
  *
  * Some callers cannot allocate device memory at all: an application whose device memory is handed
@@ -343,11 +360,15 @@ void lbpc_batch_destroy(lbpc_batch* b);
  * Returns LBPC_OK, LBPC_ENONPHYS if a node left the EOS range, LBPC_EINVAL, LBPC_ENOMEM or
  * LBPC_ECUDA.
  *
- * The call allocates nothing: no cudaMalloc, no cudaFree, no allocating library routine. The first
- * call on a device looks up the device address of the static array, with that device current; make
- * that first call before any stream capture. Every call shares the one array, which keeps the last
- * call's contents (the status word is cleared at the start of each call); calls that overlap on the
- * GPU, from several threads or streams, race on it. */
+ * The call allocates nothing itself: no cudaMalloc, no cudaFree, no allocating library routine. Every
+ * call looks up the device address of the static array in the device context that is current
+ * (cudaGetSymbolAddress; an address is never carried over, so a device reset is harmless). Under CUDA's
+ * default lazy module loading the array is placed in device memory when the library's module is
+ * first used in a context, which can be the first lbpc_step_static call on that device: that first
+ * call may therefore need about 6 MiB of free device memory, and it should come before any stream
+ * capture. Later calls need no device memory at all. Every call shares the one array, which keeps
+ * the last call's contents (the status word is cleared at the start of each call); calls that overlap
+ * on the GPU, from several threads or streams, race on it. */
 #define LBPC_STATIC_MAX_NODES (256 * 256)
 lbpc_status lbpc_step_static(const lbpc_params* p, const void* f_in, const void* g_in, void* f_out, void* g_out,
                              const double* wall_in, double* wall_out, void* phi_prev, double* rho_ave, int64_t step,

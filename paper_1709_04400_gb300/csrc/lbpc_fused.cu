@@ -78,11 +78,11 @@ static cudaError_t fused_impl(const SplitBuffers& b, const DevParams& P, int cur
   if constexpr (sizeof(S) <= 4) {  // the TMA-staged kernel exists for FP32 and FP16 storage
     if (b.tma[cur]) {
       using B = TmaBox<S, TX, TY>;
-      static bool attr = false;
-      if (!attr) {
-        cudaFuncSetAttribute(k_fused_tma<S, R, TX, TY, NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, B::BYTES);
-        attr = true;
-      }
+      // The dynamic shared-memory limit is held per device context, so it is set before every launch:
+      // the call is cheap, thread-safe, and right after a device reset or on a second device.
+      const cudaError_t e =
+          cudaFuncSetAttribute(k_fused_tma<S, R, TX, TY, NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, B::BYTES);
+      if (e != cudaSuccess) return e;
       k_fused_tma<S, R, TX, TY, NPT><<<grid, TX * TY / NPT, B::BYTES, st>>>(
           fs, gs, fd, gd, (R*)b.phi_prev, P, step, step == 0, b.scalars, b.partials, b.status, *b.tma[cur]);
       staged = true;
@@ -100,17 +100,19 @@ static cudaError_t fused_impl(const SplitBuffers& b, const DevParams& P, int cur
 }
 
 // ---- tensor maps of the TMA-staged path ----
+static PFN_cuTensorMapEncodeTiled_v12000 query_encode_fn() {
+  void* p = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    return (PFN_cuTensorMapEncodeTiled_v12000)p;
+  return nullptr;
+}
+
+// The driver's entry point is the same for every device and context; the function-local static is
+// initialised once, thread-safely.
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-  }
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = query_encode_fn();
   return fn;
 }
 

@@ -1,7 +1,6 @@
 // lbpc_step_static: one time step whose scratch lives in a fixed device array of the library, for
 // callers that cannot allocate device memory (see include/lbpc.h). The kernels are the split step's;
 // only where their scratch comes from differs.
-#include <mutex>
 #include <stdint.h>
 
 #include <cuda_runtime.h>
@@ -21,27 +20,17 @@ constexpr long long kDoubles = kPlanes * kMaxNodes + kPartials + kStatusDoubles;
 
 // The scratch itself. Every GPU that loads the library holds it (about 6 MiB) until the process exits.
 // In host code this name is only a host-side stand-in for the device symbol: its device address comes
-// from cudaGetSymbolAddress below, once per device.
+// from cudaGetSymbolAddress below, in the device context current at each call.
 static __device__ __align__(256) double g_scratch[kDoubles];
 
-constexpr int kMaxDevices = 128;
-std::mutex g_mu;
-double* g_addr[kMaxDevices];  // device address of g_scratch per device, null until set up
-
-// Device address of the scratch on the current device, set up on first use with that device current.
+// Device address of the scratch in the current device context. It is looked up on every call, not
+// cached: a device reset creates a new context in which the module, and with it the array, may sit at
+// another address. Under lazy module loading the first lookup in a context loads the module.
 cudaError_t scratch_on_current_device(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = (double*)p;
-  }
-  *out = g_addr[dev];
+  *out = (double*)p;
   return cudaSuccess;
 }
 

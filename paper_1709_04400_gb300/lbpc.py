@@ -33,7 +33,7 @@ EXPORTED = ["lbpc_version", "lbpc_check_params", "lbpc_workspace_bytes", "lbpc_e
             "lbpc_batch_add", "lbpc_batch_remove", "lbpc_batch_step", "lbpc_batch_check", "lbpc_batch_fields",
             "lbpc_batch_sums", "lbpc_batch_step_count", "lbpc_batch_set_config", "lbpc_batch_config",
             "lbpc_batch_autotune", "lbpc_batch_free_bytes", "lbpc_batch_last_error", "lbpc_batch_destroy",
-            "lbpc_set_fused_tile", "lbpc_checkpoint_bytes", "lbpc_save", "lbpc_load"]
+            "lbpc_set_fused_tile", "lbpc_checkpoint_bytes", "lbpc_save", "lbpc_load", "lbpc_fma_rate"]
 
 
 class LbpcError(RuntimeError):
@@ -99,6 +99,7 @@ def load_library(path: str = LIB_PATH):
         "lbpc_save": (ctypes.c_int, [vp, vp, ctypes.c_size_t, ctypes.c_int]),
         "lbpc_load": (ctypes.c_int, [vp, vp, ctypes.c_size_t, ctypes.c_int]),
         "lbpc_step_static": (ctypes.c_int, [P, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int64, vp]),
+        "lbpc_fma_rate": (ctypes.c_int, [ctypes.c_int32, vp, dp]),
         "lbpc_batch_instance_bytes": (ctypes.c_size_t, [P]),
         "lbpc_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]),
         "lbpc_batch_add": (ctypes.c_int, [vp, P, vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int32)]),
@@ -202,6 +203,19 @@ def eos_critical(p: Params):
     if s != LBPC_OK:
         raise LbpcError(s, "lbpc_eos_critical")
     return Tc.value, pc.value
+
+
+def fma_rate(prec=FP64, stream=None):
+    """Measured FMA throughput of the current CUDA device in FLOP/s (lbpc_fma_rate): binary64 for FP64,
+    binary32 for FP32. On PyTorch's current stream unless a torch.cuda.Stream is given."""
+    import torch
+
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    out = ctypes.c_double()
+    s = load_library().lbpc_fma_rate(int(prec), ctypes.c_void_p(st), ctypes.byref(out))
+    if s != LBPC_OK:
+        raise LbpcError(s, "lbpc_fma_rate")
+    return out.value
 
 
 def coexistence(p: Params, T: float):

@@ -105,13 +105,21 @@ class Server:
         self.results: List[Result] = []
         self.node_steps = 0
         self.chunks = 0
+        self._head = None  # (request, params, rho, T, bytes) of the head of the queue, built once
+
+    def _prepared(self, req):
+        """The head request's initial fields, parameters and arena bytes, built on the host once and kept
+        until the request is admitted or rejected (the head may wait many chunks for arena room)."""
+        if self._head is None or self._head[0] is not req:
+            case, rho, T = make_case(req, self.Tc, self.rho_v, self.rho_l)
+            p = lbpc.params_from_case(case, self.prec)
+            self._head = (req, p, rho, T, lbpc.Batch.instance_bytes(p))
+        return self._head[1:]
 
     def _admit(self, now):
         while self.pending:
             req = self.pending[0]
-            case, rho, T = make_case(req, self.Tc, self.rho_v, self.rho_l)
-            p = lbpc.params_from_case(case, self.prec)
-            need = lbpc.Batch.instance_bytes(p)
+            p, rho, T, need = self._prepared(req)
             if need > self.batch.free_bytes() - (1 << 20):  # keep a little room for the work list
                 if not self.active:  # nothing will ever free memory for it
                     self.pending.popleft()

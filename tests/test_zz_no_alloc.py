@@ -1,14 +1,19 @@
 """lbpc_step_static: the time step for callers that cannot allocate device memory.
 
-Some callers have no way to hand the library a workspace (their device memory belongs to a pool
-allocator they cannot extend, or cudaMalloc is not allowed where they run). For them
-lbpc_step_static takes only the state and keeps its scratch in a static device array of the library.
-This test calls it through the C ABI for two steps in a row. The result must match what the
-ordinary entry point (lbpc_create + lbpc_step) produces from the same start, within the parity
-tolerance the other FP64 tests use. The file is named to be collected last.
+Some callers have no way to hand the library a workspace: their device memory belongs to a pool
+allocator they cannot extend, or cudaMalloc is not allowed where they run. For them lbpc_step_static
+takes only the state and keeps its scratch in a static device array of the library.
+
+This test runs the ordinary entry point (lbpc_create + lbpc_step, split organisation) for two steps and
+takes its state before and after from checkpoints (lbpc_save, whose layout include/lbpc.h documents).
+It then calls lbpc_step_static through the C ABI twice in a row from the same start. The kernels are the
+same, so the populations, phi and the wall-row forces must agree bit for bit, in every precision the
+call accepts. The second call must leave the device's free memory unchanged. The file is named so that
+pytest collects it last.
 """
 
 import ctypes
+import struct
 
 import numpy as np
 import pytest
@@ -19,14 +24,31 @@ from .helpers import RL, RV, TC
 
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-10
+HEADER = 512
+STORE = {lbpc.FP64: 8, lbpc.FP32: 4, lbpc.DF64: 8}  # bytes per stored population
+REAL = {lbpc.FP64: 8, lbpc.FP32: 4, lbpc.DF64: 8}  # bytes per value of the arithmetic type (phi)
 
 
-def _align256(n):
-    return (n + 255) // 256 * 256
+def _sections(buf, prec, nx, ny):
+    """f, g, phi, wall and rho_ave of a checkpoint (header: magic, version, header size, lbpc_params,
+    step, rho_ave, section sizes; then f, g, phi, wall for storage without reference planes)."""
+    N = nx * ny
+    assert bytes(buf[:8]) == b"LBPCCKP1"
+    off = 16 + ctypes.sizeof(lbpc.CParams)
+    step, rho_ave = struct.unpack_from("<qd", bytes(buf[off:off + 16]))
+    pop = 9 * N * STORE[prec]
+    o = HEADER
+    f = buf[o:o + pop]
+    g = buf[o + pop:o + 2 * pop]
+    o += 2 * pop
+    phi = buf[o:o + N * REAL[prec]]
+    o += N * REAL[prec]
+    wall = buf[o:o + 4 * nx * 8]
+    return dict(f=f, g=g, phi=phi, wall=wall, step=step, rho_ave=rho_ave)
 
 
-def test_static_step_matches_workspace_step():
+@pytest.mark.parametrize("prec", [lbpc.FP64, lbpc.FP32, lbpc.DF64], ids=["fp64", "fp32", "df64"])
+def test_static_step_matches_workspace_step(prec):
     import torch
 
     from paper_1709_04400_gb300 import build
@@ -35,27 +57,24 @@ def test_static_step_matches_workspace_step():
     torch.cuda.set_device(0)
     lib = lbpc.load_library()
     case, rho, T = workloads.mixed_small(TC, RV, RL)  # walls, strip, pressure top, buoyancy
-    params = lbpc.params_from_case(case, lbpc.FP64)
-    N = params.nx * params.ny
+    params = lbpc.params_from_case(case, prec)
+    nx, ny = params.nx, params.ny
 
-    # the ordinary path: a context over a caller-owned workspace
+    # the ordinary path: a context over a caller-owned workspace, checkpointed before and after two steps
     sim = lbpc.Simulation(params)
     sim.set_path(lbpc.PATH_SPLIT)
     sim.init(rho, T)
-    mass0, _ = sim.sums()
-    # A fresh context holds its state at the start of the workspace: post-collision f, then g, each
-    # 9 N doubles rounded up to 256 bytes. Copy it into buffers this test owns.
-    pop = _align256(9 * N * 8)
-    ws = sim.workspace
-    f_a = ws[0:9 * N * 8].view(torch.float64).clone()
-    g_a = ws[pop:pop + 9 * N * 8].view(torch.float64).clone()
-    f_b = torch.empty_like(f_a)
-    g_b = torch.empty_like(g_a)
-    # wall-row forces of the previous step (none before the first): [4][nx], A/B like the populations
-    wall_a = torch.zeros(4 * params.nx, dtype=torch.float64, device="cuda")
-    wall_b = torch.empty_like(wall_a)
-    phi = torch.zeros(N, dtype=torch.float64, device="cuda")
-    rho_ave = torch.tensor([mass0 / N], dtype=torch.float64, device="cuda")
+    start = _sections(sim.save(), prec, nx, ny)
+    sim.step(2)
+    ref = _sections(sim.save(), prec, nx, ny)
+    sim.close()
+    assert start["step"] == 0 and ref["step"] == 2
+
+    dev = lambda a: torch.from_numpy(np.array(a, dtype=np.uint8)).cuda()  # noqa: E731
+    f_a, g_a, wall_a = dev(start["f"]), dev(start["g"]), dev(start["wall"])
+    f_b, g_b, wall_b = torch.empty_like(f_a), torch.empty_like(g_a), torch.empty_like(wall_a)
+    phi = torch.zeros(nx * ny * REAL[prec], dtype=torch.uint8, device="cuda")  # ignored on input at step 0
+    rho_ave = torch.tensor([start["rho_ave"]], dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
 
     c = params.to_c()
@@ -68,18 +87,17 @@ def test_static_step_matches_workspace_step():
         return lib.lbpc_step_static(ctypes.byref(c), ptr(fi), ptr(gi), ptr(fo), ptr(go), ptr(wi), ptr(wo), ptr(phi),
                                     ptr(rho_ave), k, stream)
 
-    # two calls in a row: A -> B, then B -> A
+    # two calls in a row: A -> B, then B -> A; the second must not touch the device's free memory
     assert static_step(f_a, g_a, wall_a, f_b, g_b, wall_b, 0) == lbpc.LBPC_OK
+    free_before = torch.cuda.mem_get_info()[0]
     assert static_step(f_b, g_b, wall_b, f_a, g_a, wall_a, 1) == lbpc.LBPC_OK
+    free_after = torch.cuda.mem_get_info()[0]
+    assert free_after == free_before
 
-    sim.step(2)  # the existing entry point from the same start; its state is back in the first half
-    torch.cuda.synchronize()
-    f_ref = ws[0:9 * N * 8].view(torch.float64).cpu().numpy()
-    g_ref = ws[pop:pop + 9 * N * 8].view(torch.float64).cpu().numpy()
-    f_st, g_st = f_a.cpu().numpy(), g_a.cpu().numpy()
-    assert np.max(np.abs(f_st - f_ref)) / np.max(np.abs(f_ref)) < TOL
-    assert np.max(np.abs(g_st - g_ref)) / np.max(np.abs(g_ref)) < TOL
-    sim.close()
+    for name, got in (("f", f_a), ("g", g_a), ("phi", phi), ("wall", wall_a)):
+        exp = np.frombuffer(bytes(ref[name]), dtype=np.uint8)
+        assert np.array_equal(got.cpu().numpy(), exp), name
+    assert rho_ave.item() == ref["rho_ave"]
 
 
 def test_static_step_rejects_grids_beyond_its_scratch():
