@@ -90,7 +90,7 @@ def make_case(args, Tc, rv, rl):
     from paper_1709_04400_gb300 import workloads
 
     if args.workload == "evaporation":
-        n = args.n or 256
+        n = args.n or 2048
         case, rho, T = workloads.droplet_evaporation(Tc, rv, rl, n=n, radius=40.0 * n / 256, dT_ratio=args.dT)
         prec = args.prec or "fp64"
     elif args.workload == "droplet":
@@ -181,11 +181,12 @@ def _oracle_steps(job):
     return n, time.perf_counter() - t0
 
 
-def cpu_baseline(case, rho, T, budget_s=12.0, all_budget_s=4.0):
+def cpu_baseline(case, rho, T, budget_s=12.0, all_budget_s=4.0, all_case=None):
     """The FP64 oracle as it stands, on this host, on the bench workload for a bounded time: one
-    process with one thread, then one process per host core, each stepping its own copy. The workers
-    are spawned (never forked after CUDA is initialised), with the BLAS / OpenMP pools of numpy held to
-    one thread so that the core counts are exact."""
+    process with one thread, then one process per host core, each stepping its own copy (of all_case,
+    a smaller grid of the same set-up, when given: a copy of a large grid per core would need tens of
+    GB of host memory). The workers are spawned (never forked after CUDA is initialised), with the
+    BLAS / OpenMP pools of numpy held to one thread so that the core counts are exact."""
     import multiprocessing as mp
 
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
@@ -195,14 +196,16 @@ def cpu_baseline(case, rho, T, budget_s=12.0, all_budget_s=4.0):
     with ctx.Pool(1) as pool:
         n, dt = pool.map(_oracle_steps, [(case, rho, T, budget_s)])[0]
     cores = os.cpu_count() or 1
+    ac, ar, aT = all_case or (case, rho, T)
+    Na = ac["nx"] * ac["ny"]
     with ctx.Pool(cores) as pool:
-        runs = pool.map(_oracle_steps, [(case, rho, T, all_budget_s)] * cores)
-    agg = sum(N * k / t for k, t in runs) / 1e6
+        runs = pool.map(_oracle_steps, [(ac, ar, aT, all_budget_s)] * cores)
+    agg = sum(Na * k / t for k, t in runs) / 1e6
     return {"value": N * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
             "sample": f"{n} oracle steps of the {case['nx']}x{case['ny']} workload ({dt:.1f} s, numpy FP64, 1 thread)",
-            "all_cores": {"value": agg, "unit": "MLUPS", "cores": cores,
-                          "sample": f"{cores} processes, one thread each, each stepping its own copy for "
-                                    f"{all_budget_s:.0f} s ({sum(k for k, _ in runs)} oracle steps in all)"}}
+            "all_cores": {"value": agg, "unit": "MLUPS", "cores": cores, "workload": ac["name"],
+                          "sample": f"{cores} processes, one thread each, each stepping its own copy of "
+                                    f"{ac['name']} for {all_budget_s:.0f} s ({sum(k for k, _ in runs)} oracle steps in all)"}}
 
 
 # Algorithmic HBM traffic per node and step of the fused kernel: read 9 f + 9 g, write 9 f* + 9 g*,
@@ -238,17 +241,31 @@ def _dtypes():
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels this bench
-# reports, from one-pass ncu captures of the same commands (profiles/dram_traffic.md), keyed by
-# (kernel, workload, storage). They describe the kernels as built when they were taken; a change to a
-# kernel must refresh its entry or remove it (the line then reports null).
-MEASURED_TRAFFIC = {
-    ("k_collide", "droplet_evaporation_256_dT0.1Tc", "fp64"): 14_743_040,
-    ("k_fused", "droplet_evaporation_4096_dT0.1Tc", "fp32"): 2_508_742_144,
-    ("k_collide", "droplet_evaporation_2048_dT0.1Tc", "df64"): 1_639_130_112,
-    # batched step, 32x8 tiles (variant 0): 147.9 B/node captured on 96 instances (9.8 M nodes; 145 B/node on
-    # 48), scaled by nodes to the 256 instances (27.1 M nodes)
-    ("k_batch_step", "batched_evaporation_256", "fp32", 0): 4_008_000_000,
-}
+# reports, from one-pass ncu captures of the same commands, keyed by (kernel, workload, storage). Each
+# entry carries the hash of the kernel sources it was captured on (kernel_source_hash); when the
+# sources differ from that hash the entry describes another build and the line reports null.
+MEASURED_TRAFFIC = {}
+
+
+def kernel_source_hash():
+    """First 16 hex digits of the SHA-256 of the library's CUDA sources and public header."""
+    import hashlib
+
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1709_04400_gb300", "csrc")
+    files = sorted(os.path.join(csrc, f) for f in os.listdir(csrc) if f.endswith((".cu", ".cuh", ".h")))
+    for f in files + [os.path.join(ROOT, "include", "lbpc.h")]:
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel, workload, storage):
+    """DRAM bytes per launch of kernel on workload if they were captured on the current sources, else None."""
+    e = MEASURED_TRAFFIC.get((kernel, workload, storage))
+    if e is None or e[1] != kernel_source_hash():
+        return None
+    return e[0]
 
 
 # Nominal HBM3e bandwidth of GB300 (7.9 TB/s): the second denominator of an HBM roofline fraction,
@@ -264,12 +281,148 @@ def _peak_hbm():
         return 6800.0
 
 
+def _step_times(sim, steps, warmup, flush=None):
+    """Per-kernel device times in ms of `steps` steps after `warmup` untimed ones: every step timed with
+    CUDA events on the library's stream (lbpc_step_timed). With a flush buffer, L2 is overwritten
+    before every step."""
+    import torch
+
+    def one():
+        if flush is not None:
+            with torch.cuda.stream(sim.stream):
+                flush.zero_()
+        return sim.step_timed()
+
+    for _ in range(warmup):
+        one()
+    per = {}
+    for _ in range(steps):
+        for k, v in one().items():
+            per.setdefault(k, []).append(v)
+    return per
+
+
+def _needs_flush(nodes, bytes_per_node):
+    """L2 (129 MB) is flushed between timed steps unless the step's working set is well above it."""
+    return nodes * bytes_per_node < 4 * 129e6
+
+
+def variant_line(lbpc, case, rho, T, prec, path, steps, warmup, peak_bw, bytes_per_node, flush):
+    """One storage precision of a workload, timed like the headline: MLUPS, per-kernel times and the
+    HBM fraction of the whole step at its algorithmic bytes per node."""
+    sim = lbpc.Simulation(lbpc.params_from_case(case, prec))
+    sim.set_path(path)
+    sim.init(rho, T)
+    fl = flush if _needs_flush(case["nx"] * case["ny"], bytes_per_node) else None
+    per = _step_times(sim, steps, warmup, fl)
+    sim.check()
+    sim.close()
+    N = case["nx"] * case["ny"]
+    kms = {k: sum(v) / len(v) for k, v in per.items()}
+    step_ms = sum(kms.values())
+    gbs = bytes_per_node * N / (step_ms / 1e3) / 1e9
+    return {"workload": case["name"], "value": N / (step_ms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": step_ms,
+            "kernel_ms": kms, "top_kernel": max(kms, key=kms.get),
+            "hbm": {"bytes_per_node": bytes_per_node, "achieved": gbs, "peak": peak_bw, "unit": "GB/s",
+                    "frac": gbs / peak_bw, "frac_of_nominal": gbs / NOMINAL_HBM_GBS, "of": "whole step"},
+            "l2": "flushed before every timed step" if fl is not None else "working set larger than L2, no flush",
+            "launches": len(per) * steps}
+
+
+def batch_measure(lbpc, workloads, prec, instances, steps, warmup, variant=-1, ctas=16, n=0, dT=0.1, clk_index=None):
+    """Batched workload: many uneven evaporation instances in one persistent launch per step (graph
+    replayed), against the plain path (each instance stepped on its own through lbpc_step)."""
+    import torch
+
+    p0 = lbpc.Params(nx=8, ny=8)
+    Tc, _ = lbpc.eos_critical(p0)
+    rv, rl, _ = lbpc.coexistence(p0, 0.86 * Tc)
+    if n:  # every instance the evaporation case of side n (R = 0.2 n)
+        one = workloads.droplet_evaporation(Tc, rv, rl, n=n, radius=0.2 * n, dT_ratio=dT)
+        insts = [one] * instances
+        wname = f"evaporation_{n}_x{instances}"
+    else:
+        insts = workloads.batched_evaporation(Tc, rv, rl, count=instances)
+        wname = f"batched_evaporation_{len(insts)}"
+    params = [lbpc.params_from_case(c, prec) for c, _, _ in insts]
+    nodes = sum(p.nx * p.ny for p in params)
+    arena = sum(lbpc.Batch.instance_bytes(p) for p in params) + (256 << 20)
+    b = lbpc.Batch(prec, arena, max_instances=len(insts) + 8)
+    for p, (c, r, t) in zip(params, insts):
+        b.add(p, r, t)
+    if variant >= 0:  # a fixed configuration (no tuner launches before the timed steps)
+        b.set_config(variant, ctas)
+        tuned = {"fixed": True, "variant": variant, "ctas_per_sm": ctas}
+    else:
+        tuned = b.autotune(steps_per_candidate=2)
+    b.step(warmup)
+    b.check()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(clk_index) if clk_index is not None else None
+    if clk:
+        clk.__enter__()
+    torch.cuda.synchronize()
+    ev0.record(b.stream)
+    b.step(steps)
+    ev1.record(b.stream)
+    ev1.synchronize()
+    if clk:
+        clk.__exit__(None, None, None)
+    b.check()
+    batch_s = ev0.elapsed_time(ev1) / 1e3
+    cfg = b.config()
+    b.close()
+    sims = []
+    for p, (c, r, t) in zip(params, insts):
+        sim = lbpc.Simulation(p)
+        sim.init(r, t)
+        sims.append(sim)
+    for sim in sims:
+        sim.step(warmup, sync=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for sim in sims:
+        sim.step(steps, sync=False)
+    e1.record()
+    e1.synchronize()
+    plain_s = e0.elapsed_time(e1) / 1e3
+    for sim in sims:
+        sim.check()
+        sim.close()
+    value = nodes * steps / batch_s / 1e6
+    plain = nodes * steps / plain_s / 1e6
+    peak_bw = _peak_hbm()
+    bpn = storage_bytes_per_node(prec, lbpc)
+    achieved = bpn * nodes / (batch_s / steps) / 1e9
+    prec_name = {lbpc.FP64: "fp64", lbpc.FP32: "fp32", lbpc.FP16DEV: "fp16"}[prec]
+    return {
+        "workload": wname, "instances": len(insts), "nodes": nodes, "storage": prec_name,
+        "value": value, "unit": "MLUPS", "ms_per_step": batch_s * 1e3 / steps,
+        "tile": [cfg["tile_x"], cfg["tile_y"]], "ctas_per_sm": cfg["ctas_per_sm"], "graph_chunk": cfg["graph_chunk"],
+        "autotune": tuned,
+        "plain_path": {"value": plain, "unit": "MLUPS", "ms_per_step": plain_s * 1e3 / steps,
+                       "how": "each instance stepped alone through lbpc_step (fused kernel, one launch per step)"},
+        "batched_over_plain": value / plain,
+        "hbm": {"kernel": "k_batch_step", "bytes_per_node": bpn, "achieved": achieved, "peak": peak_bw,
+                "unit": "GB/s", "frac": achieved / peak_bw, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
+                "traffic": measured_traffic("k_batch_step", wname, prec_name)},
+        "l2": "working set of %.1f GB exceeds L2" % (nodes * bpn / 1e9),
+        "launches": 2 * steps, "clocks": clk.summary() if clk else None,
+    }
+
+
+def storage_bytes_per_node(prec, lbpc):
+    """Algorithmic HBM bytes per node and step of the fused / batched step of a storage precision."""
+    return fused_bytes_per_node({lbpc.FP64: 8, lbpc.DF64: 8, lbpc.FP32: 4, lbpc.FP16DEV: 2}[prec])
+
+
 def run_native(args):
     import numpy as np
     import torch
     import torch.distributed as dist
 
-    from paper_1709_04400_gb300 import build, lbpc
+    from paper_1709_04400_gb300 import build, lbpc, workloads
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -284,6 +437,10 @@ def run_native(args):
     prec = {"fp64": lbpc.FP64, "df64": lbpc.DF64, "fp32": lbpc.FP32, "fp16": lbpc.FP16DEV}[prec_name]
     params = lbpc.params_from_case(case, prec)
     N = case["nx"] * case["ny"]
+    peak_bw = _peak_hbm()
+    bw_src = "MEASURED_PEAKS.json hbm_gbs (burst copy)"
+    pb = {lbpc.FP64: 8, lbpc.DF64: 8, lbpc.FP32: 4, lbpc.FP16DEV: 2}[prec]
+    bpn = fused_bytes_per_node(pb)
 
     def barrier():
         if ws > 1:
@@ -295,12 +452,13 @@ def run_native(args):
     if args.tile >= 0:
         sim.set_fused_tile(args.tile)
     sim.init(rho, T)
-    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-    stream = sim.stream
+    flush_buf = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    flush = flush_buf if _needs_flush(N, bpn) else None
 
     def one_step():
-        with torch.cuda.stream(stream):
-            flush.zero_()
+        if flush is not None:
+            with torch.cuda.stream(sim.stream):
+                flush.zero_()
         return sim.step_timed()
 
     for _ in range(args.warmup):
@@ -321,73 +479,44 @@ def run_native(args):
         barrier()
         wall = time.perf_counter() - t0
     clocks = clk.summary()
+    sim.check()
     dev_s = sum(step_ms) / 1e3
     dev_s, wall = max_over_ranks([dev_s, wall], ws, "cuda")
     value = aggregate_mlups(ws, N, args.steps, dev_s)
     nk = len(per_kernel)
-
-    # dominant kernel and its roofline
     avg = {k: sum(v) / len(v) for k, v in per_kernel.items()}
     top = max(avg, key=avg.get)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    pb = {lbpc.FP64: 8, lbpc.DF64: 8, lbpc.FP32: 4, lbpc.FP16DEV: 2}[prec]
-    peak_bw = float(peaks.get("hbm_gbs", 6800.0))
-    bw_src = "MEASURED_PEAKS.json hbm_gbs (burst copy)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
+    step_avg_ms = sum(avg.values())
+    hbm_step = bpn * N / (step_avg_ms / 1e3) / 1e9
+    hbm = {"bytes_per_node": bpn, "achieved": hbm_step, "peak": peak_bw, "unit": "GB/s", "frac": hbm_step / peak_bw,
+           "frac_of_nominal": hbm_step / NOMINAL_HBM_GBS, "of": "whole step", "peak_source": bw_src}
+
+    # dominant kernel and its roofline
     if prec == lbpc.FP64 and "k_collide" in avg:
+        # the binary64 step is bound by the FP64 pipe: its denominator is the FMA rate of this GPU,
+        # measured here by a probe kernel, with the clocks seen while it ran
+        with ClockSampler(local) as pclk:
+            fma64 = lbpc.fma_rate(lbpc.FP64, sim.stream) / 1e12
         fpn = collide_flops(case["lambda_mode"], all(v == 1.0 for v in case["s_g"][1:]))
-        flops = fpn * N
-        achieved = flops / (avg["k_collide"] / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": "k_collide", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
-                "frac": achieved / 1.25, "traffic": MEASURED_TRAFFIC.get(("k_collide", case["name"], prec_name)),
-                "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s, profiling recipe); 1.20 measured FMA",
-                "flops_per_node": fpn, "top_kernel": top}
+        achieved = fpn * N / (avg["k_collide"] / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_collide", "achieved": achieved, "peak": fma64, "unit": "TFLOP/s",
+                "frac": achieved / fma64, "traffic": measured_traffic("k_collide", case["name"], prec_name),
+                "peak_source": "binary64 FMA rate measured in this run (lbpc_fma_rate: 8 independent FMA chains per "
+                               "thread on every SM)", "probe_clocks": pclk.summary(),
+                "flops_per_node": fpn, "top_kernel": top, "hbm": hbm}
     elif "k_fused" in avg:
-        bytes_ = fused_bytes_per_node(pb) * N
-        achieved = bytes_ / (avg["k_fused"] / 1e3) / 1e9
+        achieved = bpn * N / (avg["k_fused"] / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": "k_fused", "achieved": achieved, "peak": peak_bw, "unit": "GB/s",
-                "frac": achieved / peak_bw, "traffic": MEASURED_TRAFFIC.get(("k_fused", case["name"], prec_name)),
+                "frac": achieved / peak_bw, "traffic": measured_traffic("k_fused", case["name"], prec_name),
                 "peak_source": bw_src, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
-                "bytes_per_node": fused_bytes_per_node(pb), "top_kernel": top}
+                "bytes_per_node": bpn, "top_kernel": top, "hbm": hbm}
     else:
-        bytes_ = collide_bytes_per_node(pb) * N
-        achieved = bytes_ / (avg["k_collide"] / 1e3) / 1e9
+        cb = collide_bytes_per_node(pb)
+        achieved = cb * N / (avg["k_collide"] / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak_bw, "unit": "GB/s",
-                "frac": achieved / peak_bw, "traffic": MEASURED_TRAFFIC.get(("k_collide", case["name"], prec_name)),
+                "frac": achieved / peak_bw, "traffic": measured_traffic("k_collide", case["name"], prec_name),
                 "peak_source": bw_src, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
-                "bytes_per_node": collide_bytes_per_node(pb), "top_kernel": top}
-
-    # the same workload in double-word arithmetic (LBPC_DF64: pairs of binary32 on the FP32 pipes, held
-    # to the FP64 parity bar by the tests), timed the same way, beside the binary64 headline
-    variants = None
-    if prec == lbpc.FP64 and not args.no_variants:
-        vsim = lbpc.Simulation(lbpc.params_from_case(case, lbpc.DF64))
-        vsim.set_path(path)
-        vsim.init(rho, T)
-        vk = {}
-
-        def vstep():
-            with torch.cuda.stream(vsim.stream):
-                flush.zero_()
-            return vsim.step_timed()
-
-        for _ in range(args.warmup):
-            vstep()
-        for _ in range(args.steps):
-            for k, v in vstep().items():
-                vk.setdefault(k, []).append(v)
-        vsim.close()
-        vms = {k: sum(v) / len(v) for k, v in vk.items()}
-        vstep_ms = sum(vms.values())
-        vtop = max(vms, key=vms.get)
-        variants = {"df64": {"value": N / (vstep_ms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": vstep_ms,
-                             "dtype": "df64 (f32 pair, 48-bit significand)", "kernel_ms": vms,
-                             "top_kernel": vtop,
-                             "top_kernel_hbm_frac": collide_bytes_per_node(8) * N / (vms[vtop] / 1e3) / 1e9 / peak_bw
-                             if vtop == "k_collide" else None}}
+                "bytes_per_node": cb, "top_kernel": top, "hbm": hbm}
 
     e2e = None
     if not args.no_e2e:
@@ -407,7 +536,7 @@ def run_native(args):
             sim2.step(1, sync=False)
             sim2.sums_async(h_sums[k])
         sim2.check()
-        out = sim2.fields()
+        sim2.fields()
         torch.cuda.synchronize()
         barrier()
         te = time.perf_counter() - t0
@@ -421,9 +550,33 @@ def run_native(args):
                        "pinned host memory, lbpc_check and lbpc_fields to host at the end"}
     sim.close()
 
+    # the other storage precisions, on rank 0 after the headline's timed region: the FP64-accurate
+    # double-word step on the same workload, the binary32 and binary16-deviation fused steps on the
+    # 4096^2 case, and the 256-instance batch against the plain path
+    variants = None
+    if rank == 0 and not args.no_variants and args.workload == "evaporation":
+        variants = {}
+        if prec == lbpc.FP64:
+            variants["df64"] = variant_line(lbpc, case, rho, T, lbpc.DF64, path, args.steps, args.warmup, peak_bw,
+                                            fused_bytes_per_node(8), flush_buf)
+            variants["df64"]["dtype"] = "df64 (f32 pair, 48-bit significand)"
+        n4 = 4096
+        c4, r4, t4 = workloads.droplet_evaporation(Tc, rv, rl, n=n4, radius=40.0 * n4 / 256, dT_ratio=args.dT)
+        for name, pv in (("fp32_4096", lbpc.FP32), ("fp16_4096", lbpc.FP16DEV)):
+            variants[name] = variant_line(lbpc, c4, r4, t4, pv, lbpc.PATH_AUTO, args.steps, args.warmup, peak_bw,
+                                          storage_bytes_per_node(pv, lbpc), flush_buf)
+            variants[name]["dtype"] = DTYPE[pv]
+        del c4, r4, t4
+        variants["batched_256"] = batch_measure(lbpc, workloads, lbpc.FP32, 256, args.steps, args.warmup,
+                                                clk_index=local)
+    del flush_buf
+
     base = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        base = cpu_baseline(case, rho, T)
+        small = None
+        if N > 512 * 512:  # the all-cores leg steps one copy per core of the 256^2 case of the same set-up
+            small = workloads.droplet_evaporation(Tc, rv, rl, n=256, radius=40.0, dT_ratio=args.dT)
+        base = cpu_baseline(case, rho, T, all_case=small)
 
     if rank == 0:
         line = {
@@ -434,11 +587,13 @@ def run_native(args):
             "config": {"workload": case["name"], "nx": case["nx"], "ny": case["ny"], "nodes": N,
                        "storage": prec_name, "parallelism": f"replicas{ws}", "path": args.path,
                        "fused_tile": args.tile if args.tile >= 0 else "library default (32x8)",
-                       "l2": "flushed before every timed step (512 MiB write); each step timed with CUDA events",
-                       "wall_ms_per_step": wall * 1e3 / args.steps},
+                       "l2": ("flushed before every timed step (512 MiB write)" if flush is not None else
+                              "working set (%.2f GB) larger than L2, no flush" % (bpn * N / 1e9)) +
+                             "; each step timed with CUDA events on the library's stream",
+                       "wall_ms_per_step": wall * 1e3 / args.steps, "kernel_source_hash": kernel_source_hash()},
             "roofline": roof, "cpu_baseline": base, "e2e": e2e, "variants": variants,
             "gpu_launches": nk * args.steps,
-            "kernel_ms": {k: sum(v) / len(v) for k, v in per_kernel.items()},
+            "kernel_ms": avg,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
@@ -447,9 +602,7 @@ def run_native(args):
 
 
 def run_batch(args):
-    """Batched workload: many uneven evaporation instances in one persistent launch per step (graph
-    replayed), against the plain path (each instance stepped on its own through lbpc_step)."""
-    import numpy as np
+    """Batched workload alone: the line of batch_measure."""
     import torch
 
     from paper_1709_04400_gb300 import build, lbpc, workloads
@@ -457,89 +610,21 @@ def run_batch(args):
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     build.build()
-    p0 = lbpc.Params(nx=8, ny=8)
-    Tc, _ = lbpc.eos_critical(p0)
-    rv, rl, _ = lbpc.coexistence(p0, 0.86 * Tc)
     prec_name = args.prec or "fp32"
     prec = {"fp64": lbpc.FP64, "fp32": lbpc.FP32, "fp16": lbpc.FP16DEV}[prec_name]
-    if args.n:  # every instance the evaporation case of side n (R = 0.2 n)
-        one = workloads.droplet_evaporation(Tc, rv, rl, n=args.n, radius=0.2 * args.n, dT_ratio=args.dT)
-        insts = [one] * args.instances
-        wname = f"evaporation_{args.n}_x{args.instances}"
-    else:
-        insts = workloads.batched_evaporation(Tc, rv, rl, count=args.instances)
-        wname = f"batched_evaporation_{len(insts)}"
-    params = [lbpc.params_from_case(c, prec) for c, _, _ in insts]
-    nodes = sum(p.nx * p.ny for p in params)
-    arena = sum(lbpc.Batch.instance_bytes(p) for p in params) + (256 << 20)
-    b = lbpc.Batch(prec, arena, max_instances=len(insts) + 8)
-    for p, (c, r, t) in zip(params, insts):
-        b.add(p, r, t)
-    if args.variant >= 0:  # a fixed configuration (no tuner launches before the timed steps)
-        b.set_config(args.variant, args.ctas)
-        tuned = {"fixed": True, "variant": args.variant, "ctas_per_sm": args.ctas}
-    else:
-        tuned = b.autotune(steps_per_candidate=2)
-    b.step(args.warmup)
-    b.check()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        torch.cuda.synchronize()
-        ev0.record(b.stream)
-        b.step(args.steps)
-        ev1.record(b.stream)
-        ev1.synchronize()
-    b.check()
-    batch_s = ev0.elapsed_time(ev1) / 1e3
-    cfg = b.config()
-    b.close()
-    # plain path: the same instances, each advanced on its own (fused kernel, one launch per step)
-    sims = []
-    for p, (c, r, t) in zip(params, insts):
-        sim = lbpc.Simulation(p)
-        sim.init(r, t)
-        sims.append(sim)
-    for sim in sims:
-        sim.step(args.warmup, sync=False)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for sim in sims:
-        sim.step(args.steps, sync=False)
-    e1.record()
-    e1.synchronize()
-    plain_s = e0.elapsed_time(e1) / 1e3
-    for sim in sims:
-        sim.check()
-        sim.close()
-    value = nodes * args.steps / batch_s / 1e6
-    plain = nodes * args.steps / plain_s / 1e6
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    peak_bw = float(peaks.get("hbm_gbs", 6800.0))
-    pb = {lbpc.FP64: 8, lbpc.FP32: 4, lbpc.FP16DEV: 2}[prec]
-    achieved = fused_bytes_per_node(pb) * nodes / (batch_s / args.steps) / 1e9
+    m = batch_measure(lbpc, workloads, prec, args.instances, args.steps, args.warmup, args.variant, args.ctas,
+                      args.n, args.dT, clk_index=local)
     line = {
-        "metric": "batched coupled flow+thermal MLUPS (aggregate)", "value": value, "unit": "MLUPS", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": batch_s * 1e3 / args.steps,
+        "metric": "batched coupled flow+thermal MLUPS (aggregate)", "value": m["value"], "unit": "MLUPS",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == lbpc.FP64 else "f32", "data": "synthetic",
-        "config": {"workload": wname, "instances": len(insts), "nodes": nodes,
-                   "storage": prec_name, "tile": [cfg["tile_x"], cfg["tile_y"]], "ctas_per_sm": cfg["ctas_per_sm"],
-                   "graph_chunk": cfg["graph_chunk"], "autotune": tuned,
-                   "l2": "working set of %.1f GB exceeds L2" % (nodes * fused_bytes_per_node(pb) / 1e9)},
-        "plain_path": {"value": plain, "unit": "MLUPS", "ms_per_step": plain_s * 1e3 / args.steps,
-                       "how": "each instance stepped alone through lbpc_step (fused kernel, one launch per step)"},
-        "batched_over_plain": value / plain,
-        "roofline": {"bound": "hbm", "kernel": "k_batch_step", "achieved": achieved, "peak": peak_bw, "unit": "GB/s",
-                     "frac": achieved / peak_bw,
-                     "traffic": MEASURED_TRAFFIC.get(("k_batch_step", wname, prec_name, tuned.get("variant", -1))),
-                     "bytes_per_node": fused_bytes_per_node(pb),
-                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS},
-        "gpu_launches": 2 * args.steps, "clocks": clk.summary(),
+        "config": {"workload": m["workload"], "instances": m["instances"], "nodes": m["nodes"],
+                   "storage": prec_name, "tile": m["tile"], "ctas_per_sm": m["ctas_per_sm"],
+                   "graph_chunk": m["graph_chunk"], "autotune": m["autotune"], "l2": m["l2"]},
+        "plain_path": m["plain_path"], "batched_over_plain": m["batched_over_plain"],
+        "roofline": dict(m["hbm"], bound="hbm"),
+        "gpu_launches": m["launches"], "clocks": m["clocks"],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -148,6 +148,53 @@ template <class R> __device__ __forceinline__ void eos(R rho, R T, const DevPara
 }
 
 // ------------------------------------------------------------------------------------------------
+// zeroth moments and the pseudopotential in binary32
+// ------------------------------------------------------------------------------------------------
+// In binary32 a plain sum of nine populations rounds up to eight times at the scale of the result.
+// Near rest the populations stand in fixed ratios to the rest population (D2Q9 flow weights: f_a = f0/4
+// on the axes, 4 f_a = f0/4 on the diagonals; thermal weights of the improved model, g0 = 5T/9 and
+// g_a = T/18 = g0/10, within a factor 2 of g0/8), and a difference of two binary32 numbers within a
+// factor 2 of each other is exact (Sterbenz). The sums below take every population relative to that ratio first, so
+// the large part is one exact product of the rest population and the rounding falls on small
+// deviations. Binary64 and double-word arithmetic keep the plain sums.
+template <class R> __device__ __forceinline__ R density_of(const R f[9]) {
+  if constexpr (sizeof(R) == 4) {
+    const R q = f[0] * 0.25f;
+    const R A = ((f[1] - q) + (f[2] - q)) + ((f[3] - q) + (f[4] - q));
+    const R B = (fmaf(4.f, f[5], -q) + fmaf(4.f, f[6], -q)) + (fmaf(4.f, f[7], -q) + fmaf(4.f, f[8], -q));
+    return fmaf(2.25f, f[0], A + B * 0.25f);  // rho = 9 f0/4 + A + B/4
+  } else {
+    return f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+  }
+}
+
+// Temperature T = sum g. In binary32 also its rounding residual lo (T + lo is the sum of the deviations
+// to within their own small roundings): the liquid's pressure changes with T about 30 times faster than
+// with rho in lattice units, so the residual is carried into psi^2 (psi_squared).
+template <class R> __device__ __forceinline__ R heat_of(const R g[9], R& lo) {
+  if constexpr (sizeof(R) == 4) {
+    const R q = g[0] * 0.125f;
+    const R E = (((g[1] - q) + (g[2] - q)) + ((g[3] - q) + (g[4] - q))) +
+                (((g[5] - q) + (g[6] - q)) + ((g[7] - q) + (g[8] - q)));
+    const R t2 = g[0] * 2.f;
+    const R T = t2 + E;  // T = 2 g0 + sum (g_a - g0/8)
+    lo = E - (T - t2);   // exact residual (Fast2Sum: |2 g0| > |E|)
+    return T;
+  } else {
+    lo = R(0);
+    return g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
+  }
+}
+
+// psi^2 = (2/G)(p_EOS - rho c_s^2) (reading of Ref. [48]), with p_EOS first moved by (dp/dT)_rho Tlo
+// for the residual of a binary32 temperature (zero otherwise).
+template <class R>
+__device__ __forceinline__ R psi_squared(R p, R dpdT, R Tlo, R rho, const Coefs<R>& C) {
+  if constexpr (sizeof(R) == 4) return C.psi_scale * ((p + dpdT * Tlo) - rho * R(1.0 / 3.0));
+  else return C.psi_scale * (p - rho * R(1.0 / 3.0));
+}
+
+// ------------------------------------------------------------------------------------------------
 // population storage
 // ------------------------------------------------------------------------------------------------
 // One population set (f or g) in one buffer: SoA [9][N] of the storage type S. With S = __half the
@@ -380,14 +427,48 @@ __device__ __forceinline__ void wall_force_store(double* wall, const DevParams& 
 // ------------------------------------------------------------------------------------------------
 // Flow MRT collision with forcing (reading of the improved pseudopotential model, Refs. [13,29]):
 // m* = m - Lambda (m - m_eq) + (I - Lambda/2) S_F, S_F with the sigma term Q in the energy moments.
+//
+// Binary32 takes the collision in increments, f* = f + M^{-1} (m* - m), so that every stored population
+// is rounded once at its own scale. Rebuilding f* from all nine post-collision moments rounds several
+// times at the scale of the populations, and the roundings of the opposite pair e_a, -e_a differ, which
+// moves momentum at random. The non-equilibrium parts m - m_eq of the energy and stress moments come
+// from the populations' exact deviations from their rest-state ratios (see density_of), not from moments
+// of size about 2 rho that cancel. Binary64 and double-word arithmetic rebuild f* from m*.
 template <class R>
 __device__ __forceinline__ void collide_flow(R f[9], R rho, R vx, R vy, R Fx, R Fy, R Q, const DevParams& P) {
   const Coefs<R>& C = coefs<R>(P);
-  R m[9];
-  to_moments(f, m);
   const R vxx = vx * vx, vyy = vy * vy;
   const R v2 = vxx + vyy;
   const R vF = vx * Fx + vy * Fy;
+  if constexpr (sizeof(R) == 4) {
+    const R q = f[0] * 0.25f;
+    const R d1 = f[1] - q, d2 = f[2] - q, d3 = f[3] - q, d4 = f[4] - q;
+    const R d5 = fmaf(4.f, f[5], -q), d6 = fmaf(4.f, f[6], -q), d7 = fmaf(4.f, f[7], -q), d8 = fmaf(4.f, f[8], -q);
+    const R A = (d1 + d2) + (d3 + d4), B = (d5 + d6) + (d7 + d8);
+    const R e_dev = A + B;                       // m1 + 2 rho
+    const R eps_dev = A * -3.f;                  // m2 - rho
+    const R pxx = (d1 + d3) - (d2 + d4);         // m7
+    const R pxy = ((d5 + d7) - (d6 + d8)) * 0.25f;  // m8
+    const R qx = (f[1] - f[3]) * -2.f + ((f[5] - f[6]) + (f[8] - f[7]));  // m4
+    const R qy = (f[2] - f[4]) * -2.f + ((f[5] - f[7]) + (f[6] - f[8]));  // m6
+    const R r3v2 = rho * v2 * 3.f;
+    R dm[9], df[9];
+    dm[0] = R(0);  // S_F,0 = 0 and m0_eq = rho
+    dm[3] = Fx;    // j* = j + F whatever s_j (m_eq,3 = j + F/2)
+    dm[5] = Fy;
+    dm[1] = C.hf[1] * (vF * 6 + Q) - C.s_f[1] * (e_dev - r3v2);  // m1 - m1_eq = (m1 + 2 rho) - 3 rho v^2
+    dm[2] = C.hf[2] * (vF * -6 - Q) - C.s_f[2] * (eps_dev + r3v2);  // m2 - m2_eq = (m2 - rho) + 3 rho v^2
+    dm[4] = C.hf[4] * -Fx - C.s_f[4] * (qx + rho * vx);
+    dm[6] = C.hf[6] * -Fy - C.s_f[6] * (qy + rho * vy);
+    dm[7] = C.hf[7] * ((vx * Fx - vy * Fy) * 2) - C.s_f[7] * (pxx - rho * (vxx - vyy));
+    dm[8] = C.hf[8] * (vx * Fy + vy * Fx) - C.s_f[8] * (pxy - rho * vx * vy);
+    from_moments(dm, df);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) f[a] = f[a] + df[a];
+    return;
+  }
+  R m[9];
+  to_moments(f, m);
   // conserved moments: m0* = m0 (S_F,0 = 0, m0_eq = rho) and j* = j + F whatever s_j (m_eq,3 = j + F/2)
   m[3] += Fx;
   m[5] += Fy;

@@ -76,13 +76,14 @@ __global__ void __launch_bounds__(BLOCK) k_macro(PopBuf<S> fsrc, PopBuf<S> gsrc,
     const int y = (int)(i / P.nx), x = (int)(i - (long long)y * P.nx);
     R f[9], g[9];
     pull_closed<S, R>(fsrc, gsrc, P, x, y, f, g);
-    const R rho = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+    const R rho = density_of(f);
     const R jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
     const R jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
-    const R T = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
+    R Tlo;
+    const R T = heat_of(g, Tlo);
     R p, dpdT, inv_rho;
     eos(rho, T, P, p, dpdT, &inv_rho);
-    const R psi2 = C.psi_scale * (p - rho * R(1.0 / 3.0));
+    const R psi2 = psi_squared(p, dpdT, Tlo, rho, C);
     const int bad = classify(rho, T, psi2, P);
     if (bad) report(status, step, x, y, bad);
     pl.p[P_RHO][i] = rho;

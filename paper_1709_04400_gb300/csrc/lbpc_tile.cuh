@@ -71,11 +71,34 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   return ok != 0;
 }
 
-// Bounded wait: about a second of polling at most; false if the phase did not complete.
+// try_wait with a suspend-time hint: a thread whose phase is incomplete sleeps (issuing nothing) until
+// the phase completes or hint_ns nanoseconds pass.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, unsigned parity, unsigned hint_ns) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait: sleeps in the barrier's own wait, woken when the phase completes, and gives up after
+// about a second of wall-clock time or 2^20 tries, whichever comes first; false if the phase did not
+// complete.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
-  for (unsigned it = 0; it < (1u << 20); ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 0; it < (1u << 20); ++it) {
+    if (mbar_try_wait_sleep(bar, parity, 100000u)) return true;
+    if (global_ns() - t0 > 1000000000ull) break;
+  }
+  return mbar_try_wait(bar, parity);
 }
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int x, int y, int z, uint64_t* bar) {
@@ -187,13 +210,14 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
     }
     const R* fk = f[k];
     const R* gk = g[k];
-    rho[k] = fk[0] + fk[1] + fk[2] + fk[3] + fk[4] + fk[5] + fk[6] + fk[7] + fk[8];
+    rho[k] = density_of(fk);
     const R jx = fk[1] - fk[3] + fk[5] - fk[6] - fk[7] + fk[8];
     const R jy = fk[2] - fk[4] + fk[5] + fk[6] - fk[7] - fk[8];
-    T[k] = gk[0] + gk[1] + gk[2] + gk[3] + gk[4] + gk[5] + gk[6] + gk[7] + gk[8];
+    R Tlo;
+    T[k] = heat_of(gk, Tlo);
     R p;
     eos(rho[k], T[k], P, p, dpdT[k]);
-    const R psi2 = C.psi_scale * (p - rho[k] * R(1.0 / 3.0));
+    const R psi2 = psi_squared(p, dpdT[k], Tlo, rho[k], C);
     if (active[k]) {
       const int bad = classify(rho[k], T[k], psi2, P);
       if (bad) report(status, step, gx, gy, bad);
@@ -230,11 +254,12 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
       const int x = wrap_any(x0 + hx - 2, P.nx), y = row_of(P, y0 + hy - 2);
       pull_closed<S, R>(fsrc, gsrc, P, x, y, fr, gr);
     }
-    const R rr = fr[0] + fr[1] + fr[2] + fr[3] + fr[4] + fr[5] + fr[6] + fr[7] + fr[8];
-    const R Tr = gr[0] + gr[1] + gr[2] + gr[3] + gr[4] + gr[5] + gr[6] + gr[7] + gr[8];
+    const R rr = density_of(fr);
+    R Trlo;
+    const R Tr = heat_of(gr, Trlo);
     R pr, dr;
     eos(rr, Tr, P, pr, dr);
-    const R psi2 = C.psi_scale * (pr - rr * R(1.0 / 3.0));
+    const R psi2 = psi_squared(pr, dr, Trlo, rr, C);
     s_rho[hy][hx] = rr;
     s_T[hy][hx] = Tr;
     s_psi[hy][hx] = sqrt(fmax(psi2, R(0)));

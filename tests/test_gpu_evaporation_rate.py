@@ -60,7 +60,7 @@ def oracle_rate():
 
 # field errors after the 4000 steps, against the oracle's final fields (max relative for rho and T,
 # relative to the largest |u| for the velocity)
-FIELD_BARS = {lbpc.FP64: 1e-10, lbpc.DF64: 1e-10, lbpc.FP32: 3e-4, lbpc.FP16DEV: 5e-2}
+FIELD_BARS = {lbpc.FP64: 1e-10, lbpc.DF64: 1e-10, lbpc.FP32: 1e-4, lbpc.FP16DEV: 5e-2}
 
 
 def _field_errors(got):

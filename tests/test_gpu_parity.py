@@ -235,9 +235,9 @@ def test_tall_channel_takes_the_split_step():
         assert np.array_equal(a, b)
     p, s = run_oracle(case, rho, T, steps)
     err = _errors(out[0], p, s)
-    # FP32 bar on rho and T; u is relative to the largest |u|, still small three steps after a start
-    # from rest, where the binary32 rounding of the momentum reaches about 1.2e-4 of it
-    assert err["rho"] <= 1e-4 and err["T"] <= 1e-4 and err["ux"] <= 2e-4 and err["uy"] <= 2e-4, err
+    # the FP32 field bar on every field (u relative to the largest |u|, which is small three steps after
+    # a start from rest)
+    assert err["rho"] <= 1e-4 and err["T"] <= 1e-4 and err["ux"] <= 1e-4 and err["uy"] <= 1e-4, err
 
 
 def test_device_pointers_and_async_steps():
@@ -325,7 +325,14 @@ def test_fused_tile_shapes(prec):
     """Every tile configuration of the fused step (32 x 16 and 32 x 8 with one node per thread, 32 x 16
     and 32 x 32 with two; TMA-staged interior tiles) computes the same step; the FP32 result stays
     within 1e-4 of the oracle. A ragged 101 x 75 grid exercises partial tiles and the plain-load path
-    (its rows are not 16-byte multiples, so no TMA)."""
+    (its rows are not 16-byte multiples, so no TMA).
+
+    The configurations with the same nodes per thread run the same code and agree bit for bit. With two
+    nodes per thread the compiler fuses some multiplies and adds differently, so the two groups agree to
+    binary32 round-off grown over the 60 steps: about 3e-5 relative in FP32. Binary16 storage turns such
+    a difference into a rounding of a stored deviation to the other side, 2^-11 of it, so the FP16 groups
+    agree to about 1e-4 (the path's own error against the oracle is 2e-2 on u)."""
+    between = 5e-5 if prec == lbpc.FP32 else 3e-4
     for case, rho, T in (workloads.droplet_periodic(TC, RV, RL), workloads.mixed_small(TC, RV, RL, nx=101, ny=75)):
         out = []
         for tile in (0, 1, 2, 3):
@@ -335,10 +342,11 @@ def test_fused_tile_shapes(prec):
             sim.step(60)
             out.append(sim.fields())
             sim.close()
-        for other in out[1:]:
-            for a, b in zip(other, out[0]):
-                # binary32 round-off of differently ordered operations, grown over 60 steps
-                assert np.max(np.abs(a - b)) <= 5e-5 * np.max(np.abs(b)) + 1e-12, case["name"]
+        for same in ((0, 1), (2, 3)):  # same nodes per thread: the same bits
+            for a, b in zip(out[same[1]], out[same[0]]):
+                assert np.array_equal(a, b), (case["name"], same)
+        for a, b in zip(out[2], out[0]):
+            assert np.max(np.abs(a - b)) <= between * np.max(np.abs(b)) + 1e-12, case["name"]
         if prec == lbpc.FP32:
             p, s = run_oracle(case, rho, T, 60)
             for o in out:
