@@ -4,10 +4,13 @@
                     [--workload evaporation|droplet|heated_wall] [--n SIDE] [--prec fp64|fp32]
 
 A bench step is one coupled time step (flow and thermal populations, every part of the hot path)
-over the whole grid. Default workload: 256 x 256 droplet evaporation (R = 40, dT = 0.1 T_c,
-Sec. IV A set-up), FP64 storage and arithmetic. Metric: coupled MLUPS (million lattice-node updates
-of f and g per second). The working set of 256^2 is smaller than L2, so L2 is flushed (a 512 MiB
-write) before every timed step and each step is timed with CUDA events on the library's stream.
+over the whole grid. Default workload: 2048 x 2048 droplet evaporation (R = 320, dT = 0.1 T_c, the
+Sec. IV A set-up scaled up), FP64 storage and arithmetic. Metric: coupled MLUPS (million lattice-node
+updates of f and g per second). Each step is timed with CUDA events on the library's stream; a grid
+whose working set is not well above L2 has L2 flushed (a 512 MiB write) before every timed step.
+The line carries the binary64 step's ALU roofline against the FMA rate measured in the same run and
+its HBM fraction, and, as variants, the double-word step on the same grid, the FP32 and FP16 fused
+steps at 4096^2 and the 256-instance batch against the plain path.
 
 Under torchrun (N > 1) each rank advances its own independent replica (weak scaling, no collective
 on the data path); value = all ranks' node updates / the slowest rank's time.
@@ -56,7 +59,9 @@ def parse(argv=None):
                          "per thread, 3 = 32x32 two per thread")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-variants", action="store_true", help="skip the double-word (DF64) variant of an FP64 run")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the variants of the evaporation line (DF64 on the same grid, FP32 and FP16 at 4096^2, "
+                         "the 256-instance batch)")
     ap.add_argument("--no-side-run", action="store_true", help="served workload: no 4096^2 FP16 run alongside")
     return ap.parse_args(argv)
 
@@ -244,7 +249,14 @@ def _dtypes():
 # reports, from one-pass ncu captures of the same commands, keyed by (kernel, workload, storage). Each
 # entry carries the hash of the kernel sources it was captured on (kernel_source_hash); when the
 # sources differ from that hash the entry describes another build and the line reports null.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    # one-pass ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of the bench's own commands
+    ("k_collide", "droplet_evaporation_2048_dT0.1Tc", "fp64"): (1_540_016_640, "b4eac5eee96759d7"),
+    ("k_collide", "droplet_evaporation_2048_dT0.1Tc", "df64"): (1_640_811_008, "b4eac5eee96759d7"),
+    ("k_fused", "droplet_evaporation_4096_dT0.1Tc", "fp32"): (2_503_675_648, "b4eac5eee96759d7"),
+    ("k_fused", "droplet_evaporation_4096_dT0.1Tc", "fp16"): (1_579_742_720, "b4eac5eee96759d7"),
+    ("k_batch_step", "batched_evaporation_256", "fp32"): (4_115_829_248, "b4eac5eee96759d7"),
+}
 
 
 def kernel_source_hash():
@@ -307,7 +319,7 @@ def _needs_flush(nodes, bytes_per_node):
     return nodes * bytes_per_node < 4 * 129e6
 
 
-def variant_line(lbpc, case, rho, T, prec, path, steps, warmup, peak_bw, bytes_per_node, flush):
+def variant_line(lbpc, case, rho, T, prec, path, steps, warmup, peak_bw, bytes_per_node, flush, storage):
     """One storage precision of a workload, timed like the headline: MLUPS, per-kernel times and the
     HBM fraction of the whole step at its algorithmic bytes per node."""
     sim = lbpc.Simulation(lbpc.params_from_case(case, prec))
@@ -321,8 +333,9 @@ def variant_line(lbpc, case, rho, T, prec, path, steps, warmup, peak_bw, bytes_p
     kms = {k: sum(v) / len(v) for k, v in per.items()}
     step_ms = sum(kms.values())
     gbs = bytes_per_node * N / (step_ms / 1e3) / 1e9
+    top = max(kms, key=kms.get)
     return {"workload": case["name"], "value": N / (step_ms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": step_ms,
-            "kernel_ms": kms, "top_kernel": max(kms, key=kms.get),
+            "kernel_ms": kms, "top_kernel": top, "top_kernel_traffic": measured_traffic(top, case["name"], storage),
             "hbm": {"bytes_per_node": bytes_per_node, "achieved": gbs, "peak": peak_bw, "unit": "GB/s",
                     "frac": gbs / peak_bw, "frac_of_nominal": gbs / NOMINAL_HBM_GBS, "of": "whole step"},
             "l2": "flushed before every timed step" if fl is not None else "working set larger than L2, no flush",
@@ -410,6 +423,27 @@ def batch_measure(lbpc, workloads, prec, instances, steps, warmup, variant=-1, c
         "l2": "working set of %.1f GB exceeds L2" % (nodes * bpn / 1e9),
         "launches": 2 * steps, "clocks": clk.summary() if clk else None,
     }
+
+
+def serve_measure(lbpc, serve, prec, requests, rate, side_lo, side_hi, steps_lo, steps_hi, clk_index=None):
+    """A Poisson stream of mixed evaporation / heated-wall requests, admitted by an HBM budget and advanced
+    together by continuous batching: p50 / p99 time-to-result and aggregate MLUPS."""
+    reqs = serve.poisson_stream(requests, rate=rate, seed=170904400 + 4, side_lo=side_lo, side_hi=side_hi,
+                                steps_lo=steps_lo, steps_hi=steps_hi)
+    srv = serve.Server(prec=prec, hbm_budget_bytes=24 << 30)
+    clk = ClockSampler(clk_index) if clk_index is not None else None
+    if clk:
+        clk.__enter__()
+    srv.run(reqs)
+    if clk:
+        clk.__exit__(None, None, None)
+    st = srv.stats()
+    srv.close()
+    return {"workload": f"served_stream_{requests}", "value": st["aggregate_mlups"], "unit": "MLUPS",
+            "latency": {"p50_s": st["p50_s"], "p99_s": st["p99_s"], "mean_s": st["mean_s"]},
+            "rate_per_s": rate, "sides": [side_lo, side_hi], "steps": [steps_lo, steps_hi],
+            "mix": "half evaporation, half heated wall", "served": st,
+            "clocks": clk.summary() if clk else None}
 
 
 def storage_bytes_per_node(prec, lbpc):
@@ -558,17 +592,23 @@ def run_native(args):
         variants = {}
         if prec == lbpc.FP64:
             variants["df64"] = variant_line(lbpc, case, rho, T, lbpc.DF64, path, args.steps, args.warmup, peak_bw,
-                                            fused_bytes_per_node(8), flush_buf)
+                                            fused_bytes_per_node(8), flush_buf, "df64")
             variants["df64"]["dtype"] = "df64 (f32 pair, 48-bit significand)"
         n4 = 4096
         c4, r4, t4 = workloads.droplet_evaporation(Tc, rv, rl, n=n4, radius=40.0 * n4 / 256, dT_ratio=args.dT)
-        for name, pv in (("fp32_4096", lbpc.FP32), ("fp16_4096", lbpc.FP16DEV)):
+        for name, pv, sname in (("fp32_4096", lbpc.FP32, "fp32"), ("fp16_4096", lbpc.FP16DEV, "fp16")):
             variants[name] = variant_line(lbpc, c4, r4, t4, pv, lbpc.PATH_AUTO, args.steps, args.warmup, peak_bw,
-                                          storage_bytes_per_node(pv, lbpc), flush_buf)
+                                          storage_bytes_per_node(pv, lbpc), flush_buf, sname)
             variants[name]["dtype"] = DTYPE[pv]
         del c4, r4, t4
         variants["batched_256"] = batch_measure(lbpc, workloads, lbpc.FP32, 256, args.steps, args.warmup,
                                                 clk_index=local)
+        # a bounded sample of the served stream (sides 64-512, 1k-5k steps, Poisson arrivals at 40 per
+        # second), FP32: continuous batching of requests that arrive while others are on the GPU
+        from paper_1709_04400_gb300 import serve
+
+        variants["served_120"] = serve_measure(lbpc, serve, lbpc.FP32, 120, 40.0, 64, 512, 1000, 5000,
+                                               clk_index=local)
     del flush_buf
 
     base = None
