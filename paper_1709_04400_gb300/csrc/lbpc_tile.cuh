@@ -71,34 +71,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   return ok != 0;
 }
 
-// try_wait with a suspend-time hint: a thread whose phase is incomplete sleeps (issuing nothing) until
-// the phase completes or hint_ns nanoseconds pass.
-__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, unsigned parity, unsigned hint_ns) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Bounded wait: sleeps in the barrier's own wait, woken when the phase completes, and gives up after
-// about a second of wall-clock time or 2^20 tries, whichever comes first; false if the phase did not
-// complete.
+// Bounded wait: about a second of polling at most; false if the phase did not complete.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
-  const unsigned long long t0 = global_ns();
-  for (unsigned it = 0; it < (1u << 20); ++it) {
-    if (mbar_try_wait_sleep(bar, parity, 100000u)) return true;
-    if (global_ns() - t0 > 1000000000ull) break;
-  }
-  return mbar_try_wait(bar, parity);
+  for (unsigned it = 0; it < (1u << 20); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
 }
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int x, int y, int z, uint64_t* bar) {
