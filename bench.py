@@ -231,10 +231,12 @@ def collide_bytes_per_node(prec_bytes):
 
 # Algorithmic FP64 operations of the split collide kernel per node (each add, subtract, multiply and
 # divide counted once; an FMA counts as its multiply and its add), counted term by term from the
-# kernel: gradients 41, source 15, flow collision 140, thermal collision 64 with unit thermal rates
-# (116 otherwise); lambda = rho c_V chi adds 20 for grad rho.
+# kernel: flow collision 136 (moments 34, equilibria and forcing 29, relaxation of 6 moments 30,
+# back-transform 41, momentum update 2); heat role 93 with unit thermal rates (gradients 41, source 14,
+# thermal collision in closed form 38); general thermal rates take the full MRT collision, 78 more;
+# lambda = rho c_V chi adds 20 for grad rho.
 def collide_flops(lambda_mode, unit_heat_rates):
-    return 259 + (20 if lambda_mode == "rho_cv_chi" else 0) + (0 if unit_heat_rates else 52)
+    return 229 + (20 if lambda_mode == "rho_cv_chi" else 0) + (0 if unit_heat_rates else 78)
 
 
 # arithmetic type of each storage precision ("df64": double-word, pairs of binary32 with a 48-bit

@@ -469,7 +469,9 @@ __device__ __forceinline__ void collide_flow(R f[9], R rho, R vx, R vy, R Fx, R 
   }
   R m[9];
   to_moments(f, m);
-  // conserved moments: m0* = m0 (S_F,0 = 0, m0_eq = rho) and j* = j + F whatever s_j (m_eq,3 = j + F/2)
+  // conserved moments: m0* = m0 = rho (S_F,0 = 0, m0_eq = rho; rho is the caller's sum of these f) and
+  // j* = j + F whatever s_j (m_eq,3 = j + F/2)
+  m[0] = rho;
   m[3] += Fx;
   m[5] += Fy;
   R meq[9], SF[9];
@@ -504,19 +506,38 @@ __device__ __forceinline__ void collide_heat(R g[9], R T, R vx, R vy, R S0, cons
     ns[0] += S0;
     ns[1] += S0 * -2;
     ns[2] += S0;
+  } else if (P.heat_unit_rates && P.model == 0) {
+    // s_k = 1 for k >= 1 (so c3 = c5 = 1/2): every non-conserved moment takes its Eq. 53 value and
+    // n* = (T + S0, -2T, 2T, T vx + (n4 + T vx)/2, -T vx, T vy + (n6 + T vy)/2, -T vy, 0, 0). Its
+    // back-transform M^{-1} n* in closed form: the axes and the diagonals share the base
+    // B = (T + S0)/9 - T/18, the axes add +-X (+-Y) with X = 5 T vx/12 + n4/12, the diagonals +-X' +-Y'
+    // with X' = T vx/6 + n4/12, and the rest population is B + T/2.
+    const R TS = T + S0;
+    const R Tvx = T * vx, Tvy = T * vy;
+    const R n4 = (g[1] - g[3]) * -2 + (g[5] - g[6] - g[7] + g[8]);
+    const R n6 = (g[2] - g[4]) * -2 + (g[5] + g[6] - g[7] - g[8]);
+    const R h4 = n4 * R(1.0 / 12.0), h6 = n6 * R(1.0 / 12.0);
+    const R X = Tvx * R(5.0 / 12.0) + h4, Xd = Tvx * R(1.0 / 6.0) + h4;
+    const R Y = Tvy * R(5.0 / 12.0) + h6, Yd = Tvy * R(1.0 / 6.0) + h6;
+    const R B = TS * R(1.0 / 9.0) - T * R(1.0 / 18.0);
+    const R P1 = B + Xd, P2 = B - Xd;
+    g[1] = B + X;
+    g[3] = B - X;
+    g[2] = B + Y;
+    g[4] = B - Y;
+    g[5] = P1 + Yd;
+    g[8] = P1 - Yd;
+    g[6] = P2 + Yd;
+    g[7] = P2 - Yd;
+    // binary32 keeps the heat of the node to one rounding (see from_moments_conserving)
+    if constexpr (sizeof(R) == 4) g[0] = TS - (((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8])));
+    else g[0] = B + T * 0.5f;
+    return;
   } else if (P.heat_unit_rates) {
-    // s_k = 1 for k >= 1: every non-conserved moment relaxes to its equilibrium, so only the zeroth
-    // moment (T) and, for Eqs. 54-55, m4 and m6 of g are needed.
-    heat_meq(T, vx, vy, P.model, ns);
+    // compromised model with s_k = 1 for k >= 1: every non-conserved moment relaxes to its equilibrium,
+    // so only the zeroth moment (T) is needed.
+    heat_meq(T, vx, vy, P.model, ns);  // Eq. 44: n7 = n8 = 0
     ns[0] = T + S0;
-    if (P.model == 0) {
-      const R n4 = (g[1] - g[3]) * -2 + (g[5] - g[6] - g[7] + g[8]);
-      const R n6 = (g[2] - g[4]) * -2 + (g[5] + g[6] - g[7] - g[8]);
-      ns[3] += C.c3 * (n4 - ns[4]);
-      ns[5] += C.c5 * (n6 - ns[6]);
-    }
-    ns[7] = R(0);
-    ns[8] = R(0);
   } else {
     R n[9], neq[9];
     to_moments(g, n);
@@ -562,6 +583,19 @@ __device__ __forceinline__ void report(long long* status, long long step, int x,
 }
 
 template <class R> __device__ __forceinline__ int classify(R rho, R T, R psi2, const DevParams& P) {
+  if constexpr (sizeof(R) == 8 && !is_dw_t<R>::value) {
+    // binary64: the same tests on the bit patterns, on the integer pipe (the FP64 pipe bounds this step).
+    // A finite double is positive exactly when its bits, read as a signed integer, are; b rho >= 1 for
+    // a positive finite b rho exactly when its bits are at least those of 1.0; -0.0 counts as >= 0.
+    const long long EXP = 0x7ff0000000000000LL;
+    const long long ir = __double_as_longlong(rho), iT = __double_as_longlong(T), ip = __double_as_longlong(psi2);
+    if ((ir & EXP) == EXP || (iT & EXP) == EXP || (ip & EXP) == EXP) return ST_NONFINITE;
+    if (ir <= 0) return ST_RHO_LE0;
+    if (__double_as_longlong(coefs<R>(P).b * rho) >= 0x3ff0000000000000LL) return ST_RHO_POLE;
+    if (iT <= 0) return ST_T_LE0;
+    if (ip < 0 && ip != (long long)0x8000000000000000ULL) return ST_PSI2_NEG;
+    return 0;
+  }
   if (!isfinite(rho) || !isfinite(T) || !isfinite(psi2)) return ST_NONFINITE;
   if (!(rho > R(0))) return ST_RHO_LE0;
   if (!(coefs<R>(P).b * rho < R(1))) return ST_RHO_POLE;
