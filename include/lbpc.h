@@ -141,14 +141,23 @@ lbpc_status lbpc_coexistence(const lbpc_params* p, double T, double* rho_v, doub
 lbpc_status lbpc_create(const lbpc_params* p, void* d_workspace, size_t bytes, void* stream, lbpc_ctx** out);
 
 /* Set the state to equilibrium populations f = M^{-1} m_eq(rho, u), g = M^{-1} m_eq(T, u), closed
- * once by the boundary step, and reset the step counter. rho, T: [ny][nx] FP64 (required);
- * ux, uy: [ny][nx] FP64 or NULL for zero. Synchronises the stream. */
+ * once by the boundary step, and reset the step counter. The thermal equilibrium is Eq. 53 for the
+ * improved model (Eq. 44 for the compromised one; the moments of Eq. 14 for Gong-Cheng); M is the
+ * MRT transform of Eqs. 42-43; the flow equilibrium is that of the delegated flow model (Sec. III B,
+ * Refs. [13,29]). The first step takes phi(t - dt) = phi(t) in Eq. 46. rho, T: [ny][nx] FP64, host
+ * memory, or device memory when on_device is nonzero (required, owned by the caller); ux, uy: [ny][nx]
+ * FP64 or NULL for zero. LBPC_EINVAL for a null rho or T, LBPC_ESTATE after an earlier error; a start
+ * outside the EOS range is reported by the first step. Synchronises the stream. */
 lbpc_status lbpc_init(lbpc_ctx* c, const double* rho, const double* T, const double* ux, const double* uy,
                       int on_device);
 
 /* Advance n >= 0 time steps and check the device status word once at the end (synchronises the
- * stream). Returns LBPC_ENONPHYS with step, x, y in lbpc_last_error if a node left the physical
- * range of the EOS during these steps. */
+ * stream). One step is the paper's coupled update (Sec. III B, the model summary after Eq. 55): the
+ * pull-stream of Eq. 47 with the boundary closures, the moments, the EOS of Eq. 56 and the
+ * pseudopotential, the interaction, adsorption and buoyancy forces, the isotropic gradients, the source
+ * of Eq. 28 with S0 of Eq. 46, the flow MRT collision with forcing and the thermal MRT collision of
+ * Eqs. 45 and 53-55. Returns LBPC_ENONPHYS with step, x, y in lbpc_last_error if a node left the
+ * physical range of the EOS during these steps; LBPC_ESTATE before lbpc_init or after an error. */
 lbpc_status lbpc_step(lbpc_ctx* c, int64_t n);
 
 /* Enqueue n time steps on the stream and return without synchronising or checking the device
