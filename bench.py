@@ -345,7 +345,7 @@ def variant_line(lbpc, case, rho, T, prec, path, steps, warmup, peak_bw, bytes_p
 
 
 def batch_measure(lbpc, workloads, prec, instances, steps, warmup, variant=-1, ctas=16, n=0, dT=0.1, clk_index=None):
-    """Batched workload: many uneven evaporation instances in one persistent launch per step (graph
+    """Batched workload: many uneven evaporation instances advanced together (lbpc_batch_step, graph
     replayed), against the plain path (each instance stepped on its own through lbpc_step)."""
     import torch
 

@@ -254,9 +254,10 @@ void lbpc_destroy(lbpc_ctx* c);
 /* ------------------------------------------------------------------------------------------------
  * Batches: many independent simulations of uneven size advancing together.
  *
- * The per-node arithmetic is the fused step's. Every instance of a batch advances in one persistent
- * launch per step: CTAs walk a device-resident work list of (instance, tile) entries, one entry per
- * tile of every instance. Steps are replayed through a captured CUDA graph in chunks when the batch
+ * The per-node arithmetic is the fused step's. A step is a few per-tile launches, one CTA per tile,
+ * each holding up to lbpc_batch_per_tile_capacity instances in its kernel parameters (the default),
+ * or one launch whose CTAs walk a device-resident work list of (instance, tile) entries (see
+ * lbpc_batch_set_config). Steps are replayed through captured CUDA graphs in chunks when the batch
  * has a non-default stream. Instances can join and leave between calls. Their parameters,
  * boundaries, sizes and step counts are their own, and an instance's result does not depend on
  * what else is in the batch. All instances of a batch share one storage precision.
@@ -272,13 +273,13 @@ size_t lbpc_batch_instance_bytes(const lbpc_params* p);
 /* Create an empty batch of at most max_instances instances in storage precision prec (LBPC_FP64,
  * LBPC_FP32 or LBPC_FP16DEV; LBPC_DF64 returns LBPC_EINVAL) over the caller's arena (256-byte
  * aligned, bytes long). Fixed descriptors take a small part of the arena. The initial configuration
- * is 32 x 16 tiles with 16 times the residency limit of CTAs launched per SM (see
- * lbpc_batch_set_config). */
+ * is 32 x 8 tiles in per-tile launches (variant 0, 0 CTAs per SM; see lbpc_batch_set_config). */
 lbpc_status lbpc_batch_create(int32_t prec, int32_t max_instances, void* d_arena, size_t bytes, void* stream,
                               lbpc_batch** out);
 
 /* Add an instance started from the equilibrium of rho, T ([ny][nx] FP64, host or device), like
- * lbpc_init. Writes its id. LBPC_ENOMEM when the arena or the slots are full. Synchronises. */
+ * lbpc_init. Writes its id. LBPC_ENOMEM when the arena or the slots are full; LBPC_EINVAL when
+ * 9 nx ny >= 2^31 (the step kernel forms population indices in 32 bits). Synchronises. */
 lbpc_status lbpc_batch_add(lbpc_batch* b, const lbpc_params* p, const double* rho, const double* T, int on_device,
                            int32_t* id);
 
@@ -300,19 +301,28 @@ lbpc_status lbpc_batch_sums(lbpc_batch* b, int32_t id, double* mass, double* hea
 int64_t lbpc_batch_step_count(const lbpc_batch* b, int32_t id);
 
 /* Step-kernel variant and CTAs launched per SM. Variants: 0 = 32x8, 1 = 32x16, 2 = 64x8 tiles with one
- * node per thread; 3 = 32x16, 4 = 64x16, 5 = 32x32 tiles with two nodes per thread. Each
- * CTA walks the work list from its index in steps of the grid size. Up to the residency limit of the
- * variant, every CTA is resident (a persistent grid). Above it, up to 64 times that limit, further
- * CTAs start as earlier ones finish, so the hardware balances tiles of uneven cost. A value above
- * that returns LBPC_EINVAL. */
+ * node per thread; 3 = 32x16, 4 = 64x16, 5 = 32x32 tiles with two nodes per thread.
+ * ctas_per_sm >= 1: one launch per step of the work-list kernel, whose CTAs walk the device work list
+ * from their index in steps of the grid size. Up to the residency limit of the variant, every CTA is
+ * resident (a persistent grid). Above it, up to 64 times that limit, further CTAs start as earlier
+ * ones finish, so the hardware balances tiles of uneven cost. A value above that returns LBPC_EINVAL.
+ * ctas_per_sm = 0: per-tile launches. A step is a sequence of launches with one CTA per tile, each over
+ * up to lbpc_batch_per_tile_capacity instances held in its kernel parameters; each launch may start
+ * while the previous one drains. A change of instances then captures the step graphs again.
+ * A negative value returns LBPC_EINVAL. */
 lbpc_status lbpc_batch_set_config(lbpc_batch* b, int32_t variant, int32_t ctas_per_sm);
+
+/* Instances one per-tile launch holds for storage precision prec (0 for a precision a batch does not
+ * take). */
+int32_t lbpc_batch_per_tile_capacity(int32_t prec);
 lbpc_status lbpc_batch_config(const lbpc_batch* b, int32_t* tile_x, int32_t* tile_y, int32_t* ctas_per_sm,
                               int32_t* graph_chunk);
 
-/* Time every variant (tile shape and nodes per thread) with 1 .. residency-limit CTAs per SM and
- * with 4, 8, 16, 32 and 64 times that limit on the batch's own instances, and keep the fastest. Every configuration computes the same
- * step, so tuning advances the batch by real steps: one warm-up plus steps_per_candidate per
- * candidate. */
+/* Time every variant (tile shape and nodes per thread) with per-tile launches, with the residency
+ * limit of CTAs per SM and with 16, 32 and 64 times that limit on the batch's own instances, and keep
+ * the fastest. Every configuration computes the same step, so tuning advances the batch by real steps:
+ * per candidate, one graph chunk of warm-up (which captures its graph), then steps_per_candidate
+ * rounded up to whole graph chunks, timed. */
 lbpc_status lbpc_batch_autotune(lbpc_batch* b, int32_t steps_per_candidate, int32_t* best_variant, int32_t* best_ctas,
                                 float* best_ms_per_step);
 

@@ -12,8 +12,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "liblbpc.so")
-SOURCES = ["lbpc_api.cu", "lbpc_split.cu", "lbpc_fused.cu", "lbpc_batch_kernels.cu", "lbpc_batch.cu", "lbpc_static.cu",
-           "lbpc_probe.cu"]
+SOURCES = ["lbpc_api.cu", "lbpc_split.cu", "lbpc_fused.cu", "lbpc_batch_kernels.cu", "lbpc_batch_tiles.cu", "lbpc_batch.cu",
+           "lbpc_static.cu", "lbpc_probe.cu"]
 HEADERS = ["lbpc_device.cuh", "lbpc_dw.cuh", "lbpc_tile.cuh", "lbpc_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -1,7 +1,9 @@
-// Host side of the batched step: many independent simulations of uneven size advance together in one
-// persistent launch per step (kernels in lbpc_fused.cu). The batch carves every instance's state out
-// of one caller-owned device arena with a first-fit allocator, keeps a tile work list on the device,
-// replays the steps through a captured CUDA graph, and picks its tile shape and CTAs per SM by timing.
+// Host side of the batched step: many independent simulations of uneven size advance together, either
+// as per-tile launches that hold the instances in their parameters (lbpc_batch_tiles.cu) or as one
+// work-list launch per step (lbpc_batch_kernels.cu). The batch carves every instance's state out of one
+// caller-owned device arena with a first-fit allocator, keeps the instance descriptors and a tile work
+// list on the device, replays the steps through captured CUDA graphs, and picks its tile shape and
+// launch form by timing.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -9,6 +11,7 @@
 
 #include <algorithm>
 #include <map>
+#include <memory>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -134,11 +137,20 @@ struct lbpc_batch {
   size_t tiles_off = 0, tiles_cap = 0;     // work list block (grows)
   std::vector<HostInst> inst;
   size_t inst_struct;  // sizeof(BatchInst<S>)
-  int variant = 1;     // tile shape (32 x 16)
-  int ctas = 2;        // CTAs launched per SM by the step kernel (set at creation)
-  int chunk = 16;      // steps per captured graph
-  cudaGraphExec_t graph = nullptr;
-  int graph_variant = -1, graph_ctas = -1, graph_ninst = -1;
+  int variant = 0;     // tile shape (32 x 8)
+  int ctas = 0;        // CTAs launched per SM by the work-list kernel; 0: per-tile launches
+  int chunk = 16;      // steps per captured graph (even: a replay leaves every buffer parity as it was)
+  // Captured graphs of `chunk` steps. The work-list kernel reads everything per instance from device
+  // memory, so one graph serves every step parity and instance set ([0]). Per-tile launches carry
+  // each instance's buffers for the parity of their step in their parameters: one graph per parity of
+  // the steps taken, captured again when the instances change.
+  struct GraphSlot {
+    cudaGraphExec_t exec = nullptr;
+    int variant = -1, ctas = -1, ninst = -1;
+    long long gen = -1;
+  } graphs[2];
+  long long gen = 0;   // bumped by every rebuild (instances or configuration changed)
+  int phase = 0;       // parity of the steps taken since creation
   bool dirty = true;   // work list needs a rebuild
   lbpc_status err = LBPC_OK;
   char msg[512] = {0};
@@ -257,6 +269,7 @@ lbpc_status rebuild(lbpc_batch* b) {
   }
   BCU(b, cudaStreamSynchronize(b->stream), "batch rebuild sync");  // host staging of the copies is released
   b->dirty = false;
+  ++b->gen;
   return LBPC_OK;
 }
 
@@ -281,33 +294,121 @@ lbpc::SplitBuffers split_view(lbpc_batch* b, const HostInst& h, char* scratch) {
   return s;
 }
 
-lbpc_status launch_direct(lbpc_batch* b, int64_t n) {
-  for (int64_t k = 0; k < n; ++k)
-    BCU(b, lbpc::batch_step_launch(b->prec, b->variant, b->ctas, (const lbpc::BatchMeta*)(b->base + b->meta_off),
-                                   b->base + b->insts_off, (int)b->inst.size(), b->stream),
-        "batch step launch");
+// One step as per-tile launches (ctas == 0): the active instances in launches of up to seg_capacity, each
+// instance reading the buffer of parity h.cur ^ rel, then the per-instance advance. Whether the step is
+// an instance's first comes from the host's count (h.step + rel), so lbpc_batch_step takes the first
+// step of new instances outside the captured graphs.
+template <class S> cudaError_t seg_step(lbpc_batch* b, int rel) {
+  constexpr int CAP = lbpc::seg_capacity<S>(), SMALL = lbpc::kSegSmall;
+  int tx, ty;
+  lbpc::batch_tile_shape(b->variant, tx, ty);
+  std::unique_ptr<lbpc::SegLaunch<S, CAP>> L(new lbpc::SegLaunch<S, CAP>());
+  std::unique_ptr<lbpc::SegLaunch<S, SMALL>> Ls(new lbpc::SegLaunch<S, SMALL>());
+  memset(L.get(), 0, sizeof(lbpc::SegLaunch<S, CAP>));
+  int launches = 0;
+  auto flush = [&]() -> cudaError_t {
+    if (L->n == 0) return cudaSuccess;
+    cudaError_t e;
+    if (L->n <= SMALL) {  // the same records in the kernel with smaller parameters
+      memset(Ls.get(), 0, sizeof(lbpc::SegLaunch<S, SMALL>));
+      Ls->n = L->n;
+      Ls->tiles = L->tiles;
+      for (int j = 0; j < L->n; ++j) {
+        Ls->first_tile[j] = L->first_tile[j];
+        Ls->in[j] = L->in[j];
+      }
+      e = lbpc::batch_seg_launch(b->prec, b->variant, true, Ls.get(), launches > 0, b->stream);
+    } else {
+      e = lbpc::batch_seg_launch(b->prec, b->variant, false, L.get(), launches > 0, b->stream);
+    }
+    ++launches;
+    L->n = 0;
+    L->tiles = 0;
+    return e;
+  };
+  for (int k = 0; k < (int)b->inst.size(); ++k) {
+    const HostInst& h = b->inst[k];
+    if (!h.used) continue;
+    if (L->n == CAP) {
+      const cudaError_t e = flush();
+      if (e != cudaSuccess) return e;
+    }
+    L->first_tile[L->n] = L->tiles;
+    lbpc::SegInst<S>& r = L->in[L->n++];
+    char* base = b->base + h.off;
+    const int c = h.cur ^ rel, d = c ^ 1;
+    const bool half = b->prec == LBPC_FP16DEV;
+    r.P = lbpc::params_of<typename lbpc::ArithOf<S>::type>(h.dp);
+    r.fs = lbpc::PopBuf<S>{(S*)(base + h.f[c]), half ? (float*)(base + h.rf[c]) : nullptr, (double*)(base + h.wall[c])};
+    r.gs = lbpc::PopBuf<S>{(S*)(base + h.g[c]), half ? (float*)(base + h.rg[c]) : nullptr, nullptr};
+    r.fd = lbpc::PopBuf<S>{(S*)(base + h.f[d]), half ? (float*)(base + h.rf[d]) : nullptr, (double*)(base + h.wall[d])};
+    r.gd = lbpc::PopBuf<S>{(S*)(base + h.g[d]), half ? (float*)(base + h.rg[d]) : nullptr, nullptr};
+    r.phi_prev = base + h.phi;
+    r.scalars = (double*)(base + h.scalars);
+    r.partials = (double*)(base + h.partials);
+    r.status = (long long*)(b->base + b->status_off) + 8 * k;
+    r.step = (const long long*)(b->base + b->insts_off + (size_t)k * b->inst_struct + offsetof(lbpc::BatchInst<S>, step));
+    r.tiles_x = (h.dp.nx + tx - 1) / tx;
+    r.first = h.step + rel == 0;
+    L->tiles += r.tiles_x * ((h.dp.ny + ty - 1) / ty);
+  }
+  const cudaError_t e = flush();
+  if (e != cudaSuccess) return e;
+  return lbpc::batch_advance_launch(b->prec, b->base + b->insts_off, (int)b->inst.size(), b->stream);
+}
+
+// One step of the current configuration; rel: parity of this step relative to the instances' h.cur.
+cudaError_t launch_step(lbpc_batch* b, int rel) {
+  if (b->ctas > 0)
+    return lbpc::batch_step_launch(b->prec, b->variant, b->ctas, (const lbpc::BatchMeta*)(b->base + b->meta_off),
+                                   b->base + b->insts_off, (int)b->inst.size(), b->stream);
+  if (b->prec == LBPC_FP64) return seg_step<double>(b, rel);
+  if (b->prec == LBPC_FP32) return seg_step<float>(b, rel);
+  return seg_step<__half>(b, rel);
+}
+
+// The host's record of m steps taken by every instance.
+void took_steps(lbpc_batch* b, int64_t m) {
+  for (auto& h : b->inst)
+    if (h.used) {
+      h.step += m;
+      h.cur ^= (int)(m & 1);
+    }
+  b->phase ^= (int)(m & 1);
+}
+
+// n steps launched one by one; rel0: parity of the first relative to the instances' h.cur.
+lbpc_status launch_direct(lbpc_batch* b, int64_t n, int rel0) {
+  for (int64_t k = 0; k < n; ++k) BCU(b, launch_step(b, (int)((rel0 + k) & 1)), "batch step launch");
   return LBPC_OK;
 }
 
-lbpc_status ensure_graph(lbpc_batch* b) {
-  if (b->graph && b->graph_variant == b->variant && b->graph_ctas == b->ctas && b->graph_ninst == (int)b->inst.size())
+lbpc_status ensure_graph(lbpc_batch* b, cudaGraphExec_t* out) {
+  const bool seg = b->ctas == 0;
+  lbpc_batch::GraphSlot& s = b->graphs[seg ? b->phase : 0];
+  if (s.exec && s.variant == b->variant && s.ctas == b->ctas && s.ninst == (int)b->inst.size() && (!seg || s.gen == b->gen)) {
+    *out = s.exec;
     return LBPC_OK;
-  if (b->graph) {
-    cudaGraphExecDestroy(b->graph);
-    b->graph = nullptr;
+  }
+  if (s.exec) {
+    cudaGraphExecDestroy(s.exec);
+    s.exec = nullptr;
   }
   cudaGraph_t g = nullptr;
   BCU(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "batch graph capture begin");
-  for (int k = 0; k < b->chunk; ++k)
-    lbpc::batch_step_launch(b->prec, b->variant, b->ctas, (const lbpc::BatchMeta*)(b->base + b->meta_off),
-                            b->base + b->insts_off, (int)b->inst.size(), b->stream);
-  BCU(b, cudaStreamEndCapture(b->stream, &g), "batch graph capture end");
-  cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaError_t le = cudaSuccess;
+  for (int k = 0; k < b->chunk && le == cudaSuccess; ++k) le = launch_step(b, k & 1);
+  const cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
+  BCU(b, le, "batch graph capture launch");
+  BCU(b, ce, "batch graph capture end");
+  cudaError_t e = cudaGraphInstantiate(&s.exec, g, 0);
   cudaGraphDestroy(g);
   BCU(b, e, "batch graph instantiate");
-  b->graph_variant = b->variant;
-  b->graph_ctas = b->ctas;
-  b->graph_ninst = (int)b->inst.size();
+  s.variant = b->variant;
+  s.ctas = b->ctas;
+  s.ninst = (int)b->inst.size();
+  s.gen = b->gen;
+  *out = s.exec;
   return LBPC_OK;
 }
 
@@ -363,10 +464,8 @@ LBPC_API lbpc_status lbpc_batch_create(int32_t prec, int32_t max_instances, void
       delete b;
       return LBPC_ECUDA;
     }
-    // default: 16 times the residency limit, the grid the autotuner picks or comes within a few per
-    // cent of on uneven instance mixes (the hardware balances tiles of uneven cost)
-    const int occ = lbpc::batch_max_ctas_per_sm(prec, b->variant);
-    b->ctas = 16 * std::max(1, occ);
+    // default: per-tile launches of 32 x 8 tiles, the fastest configuration measured on uneven
+    // instance mixes and on large instances in FP32, FP16 and FP64
     if (rebuild(b) != LBPC_OK) {
       delete b;
       return LBPC_ECUDA;
@@ -384,6 +483,8 @@ LBPC_API lbpc_status lbpc_batch_add(lbpc_batch* b, const lbpc_params* p, const d
   char why[256];
   if (lbpc_check_params(p, why, sizeof why) != LBPC_OK) return bfail(b, LBPC_EINVAL, "lbpc_batch_add: %s", why);
   if (p->prec != b->prec) return bfail(b, LBPC_EINVAL, "lbpc_batch_add: prec %d differs from the batch's %d", p->prec, b->prec);
+  if (9LL * p->nx * p->ny > 2147483647LL)  // the step kernel forms population indices in 32 bits
+    return bfail(b, LBPC_EINVAL, "lbpc_batch_add: %d x %d nodes exceed a batch instance's 9 nx ny < 2^31", p->nx, p->ny);
   int slot = -1;
   for (int k = 0; k < (int)b->inst.size(); ++k)
     if (!b->inst[k].used) {
@@ -450,21 +551,29 @@ LBPC_API lbpc_status lbpc_batch_step(lbpc_batch* b, int64_t n) {
     if (r != LBPC_OK) return r;
   }
   int64_t left = n;
-  if (b->stream && n >= b->chunk) {
-    lbpc_status r = ensure_graph(b);
+  if (left > 0 && b->ctas == 0) {  // per-tile launches take an instance's first step outside the graphs
+    bool fresh = false;
+    for (auto& h : b->inst) fresh |= h.used && h.step == 0;
+    if (fresh) {
+      lbpc_status r = launch_direct(b, 1, 0);
+      if (r != LBPC_OK) return r;
+      took_steps(b, 1);
+      left -= 1;
+    }
+  }
+  if (b->stream && left >= b->chunk) {
+    cudaGraphExec_t exec = nullptr;
+    lbpc_status r = ensure_graph(b, &exec);
     if (r != LBPC_OK) return r;
     while (left >= b->chunk) {
-      BCU(b, cudaGraphLaunch(b->graph, b->stream), "batch graph launch");
+      BCU(b, cudaGraphLaunch(exec, b->stream), "batch graph launch");
+      took_steps(b, b->chunk);
       left -= b->chunk;
     }
   }
-  lbpc_status r = launch_direct(b, left);
+  lbpc_status r = launch_direct(b, left, 0);
   if (r != LBPC_OK) return r;
-  for (auto& h : b->inst)
-    if (h.used) {
-      h.step += n;
-      h.cur ^= (int)(n & 1);
-    }
+  took_steps(b, left);
   return LBPC_OK;
 }
 
@@ -536,7 +645,7 @@ LBPC_API int64_t lbpc_batch_step_count(const lbpc_batch* b, int32_t id) {
 }
 
 LBPC_API lbpc_status lbpc_batch_set_config(lbpc_batch* b, int32_t variant, int32_t ctas_per_sm) {
-  if (!b || variant < 0 || variant >= lbpc::kBatchVariants || ctas_per_sm < 1) return LBPC_EINVAL;
+  if (!b || variant < 0 || variant >= lbpc::kBatchVariants || ctas_per_sm < 0) return LBPC_EINVAL;
   DevGuard g(b->device);
   const int occ = lbpc::batch_max_ctas_per_sm(b->prec, variant);
   if (occ < 1 || ctas_per_sm > 64 * occ)
@@ -572,23 +681,25 @@ LBPC_API lbpc_status lbpc_batch_autotune(lbpc_batch* b, int32_t steps_per_candid
   BCU(b, cudaEventCreate(&e1), "autotune event");
   float best = 1e30f;
   int bv = b->variant, bc = b->ctas;
+  // whole graph chunks, so that every candidate is timed as lbpc_batch_step runs long step counts
+  const int64_t timed = ((int64_t)std::max(steps_per_candidate, 1) + b->chunk - 1) / b->chunk * b->chunk;
   for (int v = 0; v < lbpc::kBatchVariants; ++v) {
     const int occ = lbpc::batch_max_ctas_per_sm(b->prec, v);
-    std::vector<int> cand;
-    for (int c = 1; c <= std::min(occ, 4); ++c) cand.push_back(c);  // persistent grids
-    for (int m : {4, 8, 16, 32, 64}) cand.push_back(m * occ);       // oversubscribed grids
+    // per-tile launches, the persistent grid, and grids of 16, 32 and 64 times it (the hardware then
+    // balances tiles of uneven cost)
+    std::vector<int> cand{0, occ, 16 * occ, 32 * occ, 64 * occ};
     for (int c : cand) {
       if (lbpc_batch_set_config(b, v, c) != LBPC_OK) continue;
       // every configuration computes the same step, so tuning advances the batch for real
-      if (lbpc_batch_step(b, 1) != LBPC_OK) break;  // warm-up
+      if (lbpc_batch_step(b, b->chunk) != LBPC_OK) break;  // warm-up: captures this candidate's graph
       BCU(b, cudaEventRecord(e0, b->stream), "autotune record");
-      lbpc_status r = lbpc_batch_step(b, steps_per_candidate);
+      lbpc_status r = lbpc_batch_step(b, timed);
       BCU(b, cudaEventRecord(e1, b->stream), "autotune record");
       BCU(b, cudaEventSynchronize(e1), "autotune sync");
       if (r != LBPC_OK) break;
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
-      ms /= steps_per_candidate;
+      ms /= (float)timed;
       if (ms < best) {
         best = ms;
         bv = v;
@@ -605,15 +716,23 @@ LBPC_API lbpc_status lbpc_batch_autotune(lbpc_batch* b, int32_t steps_per_candid
   return r;
 }
 
+LBPC_API int32_t lbpc_batch_per_tile_capacity(int32_t prec) {
+  if (prec == LBPC_FP64) return lbpc::seg_capacity<double>();
+  if (prec == LBPC_FP32) return lbpc::seg_capacity<float>();
+  if (prec == LBPC_FP16DEV) return lbpc::seg_capacity<__half>();
+  return 0;
+}
+
 LBPC_API size_t lbpc_batch_free_bytes(const lbpc_batch* b) { return b ? b->arena.free_bytes() : 0; }
 
 LBPC_API const char* lbpc_batch_last_error(const lbpc_batch* b) { return b ? b->msg : "null batch"; }
 
 LBPC_API void lbpc_batch_destroy(lbpc_batch* b) {
   if (!b) return;
-  if (b->graph) {
+  {
     DevGuard g(b->device);
-    cudaGraphExecDestroy(b->graph);
+    for (auto& s : b->graphs)
+      if (s.exec) cudaGraphExecDestroy(s.exec);
   }
   delete b;
 }

@@ -65,26 +65,27 @@ __global__ void __launch_bounds__(TX* TY / NPT, fused_min_blocks<S, TX * TY / NP
   __shared__ FusedSmem<R, TX, TY> sm;
   __shared__ BatchInst<S> sI[2];
   __shared__ BatchTile st[3];  // this tile's entry, the next one's, and the one after (filled while computing)
-  // walk state (work-list position, descriptor slot, ring position), kept in shared memory so that no
-  // register holds it across the tile body
-  __shared__ int s_t, s_slot, s_r;
+  // walk state (work-list position, descriptor slot, ring position) and the list length, kept in shared
+  // memory so that no register holds them across the tile body
+  __shared__ int s_t, s_slot, s_r, s_n;
   const int G = gridDim.x;
-  if ((int)blockIdx.x >= meta->ntiles) return;
   if (threadIdx.x == 0) {
     const int t0 = blockIdx.x, n = meta->ntiles;
-    st[0] = meta->tiles[t0];
+    s_n = n;
+    if (t0 < n) st[0] = meta->tiles[t0];
     if (t0 + G < n) st[1] = meta->tiles[t0 + G];
     s_t = t0;
     s_slot = 0;
     s_r = 0;
   }
   __syncthreads();
+  if ((int)blockIdx.x >= s_n) return;
   desc_copy_async<S, R>(&sI[0], &insts[st[0].inst]);
   cp_async_wait_all();
   __syncthreads();
   for (;;) {
     {
-      const int t = s_t, slot = s_slot, r = s_r, ntiles = meta->ntiles;
+      const int t = s_t, slot = s_slot, r = s_r, ntiles = s_n;
       const BatchTile tile = st[r];
       const int rn = r == 2 ? 0 : r + 1, ra = rn == 2 ? 0 : rn + 1;
       const bool more = t + G < ntiles;
@@ -96,16 +97,17 @@ __global__ void __launch_bounds__(TX* TY / NPT, fused_min_blocks<S, TX * TY / NP
       const long long step = I.step;
       const bool interior = tile.x0 >= 3 && tile.x0 + TX + 3 <= P.nx && tile.y0 >= 3 && tile.y0 + TY + 3 <= P.ny;
       if (interior)
-        fused_body<1, S, R, TX, TY, NPT>(I.f[cur], I.g[cur], I.f[cur ^ 1], I.g[cur ^ 1], (R*)I.phi_prev, P, step,
+        fused_body<1, S, R, TX, TY, NPT, true>(I.f[cur], I.g[cur], I.f[cur ^ 1], I.g[cur ^ 1], (R*)I.phi_prev, P, step,
                                          step == 0, I.scalars, I.partials, I.status, sm, tile.x0, tile.y0, tile.pslot);
       else
-        fused_body<0, S, R, TX, TY, NPT>(I.f[cur], I.g[cur], I.f[cur ^ 1], I.g[cur ^ 1], (R*)I.phi_prev, P, step,
+        fused_body<0, S, R, TX, TY, NPT, true>(I.f[cur], I.g[cur], I.f[cur ^ 1], I.g[cur ^ 1], (R*)I.phi_prev, P, step,
                                          step == 0, I.scalars, I.partials, I.status, sm, tile.x0, tile.y0, tile.pslot);
     }
+    // The CTA's last tile: it issued no copy, so its threads leave without waiting for one another.
+    if (s_t + G >= s_n) return;
     cp_async_wait_all();
     __syncthreads();  // the tile is done with the shared memory; the next descriptor and entry have landed
     const int t = s_t, r = s_r, rn = r == 2 ? 0 : r + 1;
-    if (t + G >= meta->ntiles) break;
     const bool change = st[rn].inst != st[r].inst;
     __syncthreads();  // every thread has read the walk state
     if (threadIdx.x == 0) {
@@ -157,6 +159,14 @@ static cudaError_t batch_launch_p(int variant, int ctas, const BatchMeta* d_meta
     case 5: return batch_launch_t<S, R, 32, 32, 2>(ctas, d_meta, d_insts, ninst, st);
     default: return batch_launch_t<S, R, 32, 8, 1>(ctas, d_meta, d_insts, ninst, st);
   }
+}
+
+cudaError_t batch_advance_launch(int prec, void* d_insts, int ninst, cudaStream_t st) {
+  if (ninst <= 0) return cudaSuccess;
+  if (prec == 0) k_batch_advance<double><<<ninst, 128, 0, st>>>((BatchInst<double>*)d_insts);
+  else if (prec == 1) k_batch_advance<float><<<ninst, 128, 0, st>>>((BatchInst<float>*)d_insts);
+  else k_batch_advance<__half><<<ninst, 128, 0, st>>>((BatchInst<__half>*)d_insts);
+  return cudaGetLastError();
 }
 
 cudaError_t batch_step_launch(int prec, int variant, int ctas, const BatchMeta* d_meta, void* d_insts, int ninst,

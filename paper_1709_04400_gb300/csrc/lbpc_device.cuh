@@ -9,7 +9,9 @@
 
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "lbpc_dw.cuh"
 
@@ -65,6 +67,33 @@ template <> __host__ __device__ __forceinline__ const Coefs<double>& coefs<doubl
 template <> __host__ __device__ __forceinline__ const Coefs<float>& coefs<float>(const DevParams& P) { return P.cf; }
 template <> __host__ __device__ __forceinline__ const Coefs<dw>& coefs<dw>(const DevParams& P) { return P.cw; }
 
+// The header of DevParams with the one coefficient set of arithmetic R: what a kernel of that arithmetic
+// reads, in a third of the bytes, for parameters that are copied per launch (the batch's per-tile
+// launches). The device helpers take either form (template parameter PT).
+template <class R> struct alignas(16) DevParamsOf {
+  int nx, ny;
+  long long N;
+  int yper;
+  int ybc_lo, ybc_hi;
+  int tbc[4];
+  int strip_x0, strip_x1;
+  int model;
+  int lambda_mode;
+  int buoyancy;
+  int heat_unit_rates;
+  alignas(16) Coefs<R> c;
+};
+static_assert(offsetof(DevParamsOf<float>, c) == offsetof(DevParams, cd) &&
+                  offsetof(DevParamsOf<float>, heat_unit_rates) == offsetof(DevParams, heat_unit_rates),
+              "DevParamsOf repeats the header of DevParams");
+template <class R> __host__ __device__ __forceinline__ const Coefs<R>& coefs(const DevParamsOf<R>& P) { return P.c; }
+template <class R> inline DevParamsOf<R> params_of(const DevParams& P) {
+  DevParamsOf<R> q;
+  memcpy(&q, &P, offsetof(DevParams, cd));  // the common header
+  q.c = coefs<R>(P);
+  return q;
+}
+
 // ------------------------------------------------------------------------------------------------
 // moment transforms: m = M x and x = M^{-1} m with M^{-1} = M^T diag(1/9,1/36,1/36,1/6,1/12,1/6,1/12,1/4,1/4)
 // ------------------------------------------------------------------------------------------------
@@ -118,7 +147,7 @@ template <class R> __device__ __forceinline__ void from_moments_conserving(const
 // ------------------------------------------------------------------------------------------------
 // Peng-Robinson EOS (Eq. 56) and (dp/dT)_rho
 // ------------------------------------------------------------------------------------------------
-template <class R> __device__ __forceinline__ void eos(R rho, R T, const DevParams& P, R& p, R& dpdT, R* inv_rho = nullptr) {
+template <class R, class PT> __device__ __forceinline__ void eos(R rho, R T, const PT& P, R& p, R& dpdT, R* inv_rho = nullptr) {
   const Coefs<R>& C = coefs<R>(P);
   // theta(T) = [1 + kappa (1 - sqrt(T/T_c))]^2 and d theta/dT = -kappa [..] / sqrt(T T_c); one rsqrt
   // gives both sqrt(T/T_c) = t rsqrt(t) and 1/sqrt(T T_c) = rsqrt(t) / T_c with t = T/T_c.
@@ -221,29 +250,45 @@ __host__ __device__ __forceinline__ long long wall_doubles(int nx) { return 4LL 
 template <class S> struct is_half_t { static constexpr bool value = false; };
 template <> struct is_half_t<__half> { static constexpr bool value = true; };
 
-template <class S, class R>
-__device__ __forceinline__ R pop_load(const PopBuf<S>& b, long long N, int a, long long idx, const R* w) {
+// IX is the index type: long long in general; int where the caller guarantees that every population
+// index of the buffer (9 N) fits in 31 bits, which turns each address into one 32-bit multiply-add.
+template <class S, class R, class IX = long long>
+__device__ __forceinline__ R pop_load(const PopBuf<S>& b, IX N, int a, IX idx, const R* w) {
   if constexpr (is_half_t<S>::value) {
-    return R(__half2float(__ldg(b.p + (long long)a * N + idx))) + w[a] * R(__ldg(b.ref + idx));
+    return R(__half2float(__ldg(b.p + ((IX)a * N + idx)))) + w[a] * R(__ldg(b.ref + idx));
   } else if constexpr (is_dw_t<S>::value) {
-    return R(ldgv(b.p + (long long)a * N + idx));
+    return R(ldgv(b.p + ((IX)a * N + idx)));
   } else {
-    return R(__ldg(b.p + (long long)a * N + idx));
+    return R(__ldg(b.p + ((IX)a * N + idx)));
   }
 }
 
 // Store the post-collision populations v of node i; refval is the node's zeroth moment after the
 // collision (rho for f, T + S0 for g), the reference of the FP16 deviation.
-template <class S, class R>
-__device__ __forceinline__ void pop_store(const PopBuf<S>& b, long long N, long long i, const R v[9], R refval,
-                                          const R* w) {
+template <class S, class R, class IX = long long>
+__device__ __forceinline__ void pop_store(const PopBuf<S>& b, IX N, IX i, const R v[9], R refval, const R* w) {
   if constexpr (is_half_t<S>::value) {
 #pragma unroll
-    for (int a = 0; a < 9; ++a) b.p[(long long)a * N + i] = __float2half_rn(float(v[a] - w[a] * refval));
+    for (int a = 0; a < 9; ++a) b.p[(IX)a * N + i] = __float2half_rn(float(v[a] - w[a] * refval));
     b.ref[i] = float(refval);
   } else {
 #pragma unroll
-    for (int a = 0; a < 9; ++a) b.p[(long long)a * N + i] = (S)v[a];
+    for (int a = 0; a < 9; ++a) b.p[(IX)a * N + i] = (S)v[a];
+  }
+}
+
+// pop_store through explicitly global stores, for buffer pointers that the compiler cannot place in
+// the global space (descriptors read from shared memory).
+template <class S, class R, class IX = long long>
+__device__ __forceinline__ void pop_store_global(const PopBuf<S>& b, IX N, IX i, const R v[9], R refval,
+                                                 const R* w) {
+  if constexpr (is_half_t<S>::value) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) __stwb(b.p + ((IX)a * N + i), __float2half_rn(float(v[a] - w[a] * refval)));
+    __stwb(b.ref + i, float(refval));
+  } else {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) __stwb(b.p + ((IX)a * N + i), (S)v[a]);
   }
 }
 
@@ -261,7 +306,7 @@ struct PullSrc {
   int col[3];  // x + 1, x, x - 1 (wrapped)
   int row[3];  // y + 1, y, y - 1 (wrapped when y is periodic; -1 beyond a non-periodic y edge)
 };
-__device__ __forceinline__ PullSrc pull_src(const DevParams& P, int x, int y) {
+template <class PT> __device__ __forceinline__ PullSrc pull_src(const PT& P, int x, int y) {
   PullSrc s;
   s.col[0] = x == P.nx - 1 ? 0 : x + 1;
   s.col[1] = x;
@@ -272,18 +317,18 @@ __device__ __forceinline__ PullSrc pull_src(const DevParams& P, int x, int y) {
   return s;
 }
 
-template <class S, class R>
-__device__ __forceinline__ void pull_from(const PopBuf<S>& src, const R* w, const DevParams& P, const PullSrc& s,
+template <class S, class R, class IX = long long, class PT = DevParams>
+__device__ __forceinline__ void pull_from(const PopBuf<S>& src, const R* w, const PT& P, const PullSrc& s,
                                           R v[9]) {
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     const int r = s.row[EY(a) + 1];
-    v[a] = r >= 0 ? pop_load<S, R>(src, P.N, a, (long long)r * P.nx + s.col[EX(a) + 1], w) : R(0);
+    v[a] = r >= 0 ? pop_load<S, R, IX>(src, (IX)P.N, a, (IX)r * P.nx + s.col[EX(a) + 1], w) : R(0);
   }
 }
 
-template <class S, class R>
-__device__ __forceinline__ void pull(const PopBuf<S>& src, const R* w, const DevParams& P, int x, int y, R v[9]) {
+template <class S, class R, class PT>
+__device__ __forceinline__ void pull(const PopBuf<S>& src, const R* w, const PT& P, int x, int y, R v[9]) {
   pull_from<S, R>(src, w, P, pull_src(P, x, y), v);
 }
 
@@ -291,8 +336,8 @@ __device__ __forceinline__ void pull(const PopBuf<S>& src, const R* w, const Dev
 // being the wall row's force of the step that stored the populations (`wall`, see PopBuf), so that the
 // forcing scheme's velocity v = (j + F/2)/rho vanishes on the wall (a null `wall` reads as F = 0).
 // Pressure: rho = rho_bc, u_x = 0.
-template <class R>
-__device__ __forceinline__ void flow_closure(R f[9], const DevParams& P, int x, int y, const double* wall) {
+template <class R, class PT>
+__device__ __forceinline__ void flow_closure(R f[9], const PT& P, int x, int y, const double* wall) {
   if (P.yper) return;
   const Coefs<R>& C = coefs<R>(P);
   const R d13 = f[1] - f[3];
@@ -356,7 +401,7 @@ template <class R> __device__ __forceinline__ void heat_meq(R T, R vx, R vy, int
 // g_a = -g_opp(a) + 2 g_a^eq(T_bc, 0) where the edge holds T_bc (anti-bounce-back; heat enters through
 // the wall), g_a = g_opp(a) otherwise (zero heat flux). A Dirichlet edge of a periodic axis (a ring
 // inside a periodic domain) resets the node to g := M^{-1} m_eq(T_bc, 0): x edges, then y edges.
-template <class R> __device__ __forceinline__ void heat_closure(R g[9], const DevParams& P, int x, int y) {
+template <class R, class PT> __device__ __forceinline__ void heat_closure(R g[9], const PT& P, int x, int y) {
   const Coefs<R>& C = coefs<R>(P);
   if (!P.yper) {
     if (y == 0) {
@@ -401,20 +446,20 @@ template <class R> __device__ __forceinline__ void heat_closure(R g[9], const De
 }
 
 // Post-stream, post-boundary f and g at (x, y).
-template <class S, class R>
-__device__ __forceinline__ void pull_closed(const PopBuf<S>& fsrc, const PopBuf<S>& gsrc, const DevParams& P, int x,
+template <class S, class R, class IX = long long, class PT = DevParams>
+__device__ __forceinline__ void pull_closed(const PopBuf<S>& fsrc, const PopBuf<S>& gsrc, const PT& P, int x,
                                             int y, R f[9], R g[9]) {
   const Coefs<R>& C = coefs<R>(P);
   const PullSrc src = pull_src(P, x, y);  // f and g read the same nine source nodes
-  pull_from<S, R>(fsrc, C.wf, P, src, f);
-  pull_from<S, R>(gsrc, C.wg, P, src, g);
+  pull_from<S, R, IX>(fsrc, C.wf, P, src, f);
+  pull_from<S, R, IX>(gsrc, C.wg, P, src, g);
   flow_closure(f, P, x, y, fsrc.wall);
   heat_closure(g, P, x, y);
 }
 
 // Keep the force of a wall-row node for the next step's closure (into the destination flow buffer).
-template <class R>
-__device__ __forceinline__ void wall_force_store(double* wall, const DevParams& P, int x, int y, R Fx, R Fy) {
+template <class R, class PT>
+__device__ __forceinline__ void wall_force_store(double* wall, const PT& P, int x, int y, R Fx, R Fy) {
   if (P.yper || !wall) return;
   const int edge = (y == 0 && P.ybc_lo == BC_WALL) ? 0 : (y == P.ny - 1 && P.ybc_hi == BC_WALL) ? 1 : -1;
   if (edge < 0) return;
@@ -434,8 +479,8 @@ __device__ __forceinline__ void wall_force_store(double* wall, const DevParams& 
 // moves momentum at random. The non-equilibrium parts m - m_eq of the energy and stress moments come
 // from the populations' exact deviations from their rest-state ratios (see density_of), not from moments
 // of size about 2 rho that cancel. Binary64 and double-word arithmetic rebuild f* from m*.
-template <class R>
-__device__ __forceinline__ void collide_flow(R f[9], R rho, R vx, R vy, R Fx, R Fy, R Q, const DevParams& P) {
+template <class R, class PT>
+__device__ __forceinline__ void collide_flow(R f[9], R rho, R vx, R vy, R Fx, R Fy, R Q, const PT& P) {
   const Coefs<R>& C = coefs<R>(P);
   const R vxx = vx * vx, vyy = vy * vy;
   const R v2 = vxx + vyy;
@@ -491,8 +536,8 @@ __device__ __forceinline__ void collide_flow(R f[9], R rho, R vx, R vy, R Fx, R 
 
 // Thermal MRT collision of the improved model: Eq. 45 with m_eq of Eq. 53 and S = (S0, 0, ..., 0)
 // (Eq. 46), then m3* += (1 - s3/2) s4 (m4 - m4_eq) and m5* += (1 - s5/2) s6 (m6 - m6_eq) (Eqs. 54-55).
-template <class R>
-__device__ __forceinline__ void collide_heat(R g[9], R T, R vx, R vy, R S0, const DevParams& P, R tau_inv = R(0)) {
+template <class R, class PT>
+__device__ __forceinline__ void collide_heat(R g[9], R T, R vx, R vy, R S0, const PT& P, R tau_inv = R(0)) {
   const Coefs<R>& C = coefs<R>(P);
   R ns[9];
   if (P.model == 2) {
@@ -582,7 +627,7 @@ __device__ __forceinline__ void report(long long* status, long long step, int x,
   }
 }
 
-template <class R> __device__ __forceinline__ int classify(R rho, R T, R psi2, const DevParams& P) {
+template <class R, class PT> __device__ __forceinline__ int classify(R rho, R T, R psi2, const PT& P) {
   if constexpr (sizeof(R) == 8 && !is_dw_t<R>::value) {
     // binary64: the same tests on the bit patterns, on the integer pipe (the FP64 pipe bounds this step).
     // A finite double is positive exactly when its bits, read as a signed integer, are; b rho >= 1 for

@@ -113,6 +113,48 @@ inline int batch_nodes_per_thread(int v) { return v >= 3 && v < kBatchVariants ?
 // Enqueue one batched step (persistent step kernel + per-instance advance) on st.
 cudaError_t batch_step_launch(int prec, int variant, int ctas, const BatchMeta* d_meta, void* d_insts, int ninst,
                               cudaStream_t st);
+
+// Per-tile launches of a batched step (the configuration with 0 CTAs per SM): one CTA per tile, and the
+// instances of a launch in its kernel parameters, so that the tile body reads every per-instance value
+// and buffer pointer as a uniform operand, as the single-instance kernel does. A step is a sequence of
+// such launches over the active instances (up to seg_capacity each), then the per-instance advance.
+template <class S> struct ArithOf { using type = float; };  // arithmetic of a storage type in a batch
+template <> struct ArithOf<double> { using type = double; };
+template <class S> struct alignas(16) SegInst {
+  DevParamsOf<typename ArithOf<S>::type> P;  // header and the one coefficient set the kernel reads
+  PopBuf<S> fs, gs, fd, gd;  // this launch's source and destination populations
+  void* phi_prev;            // arithmetic type
+  double* scalars;
+  double* partials;
+  long long* status;
+  const long long* step;     // the instance's step counter (in its device descriptor), read to report
+  int tiles_x;               // tiles per row
+  int first;                 // the instance's first step (its source term starts from phi itself)
+};
+constexpr size_t kSegParamBytes = 32000;  // within the 32,764 bytes of kernel parameters
+template <class S> constexpr int seg_capacity() {
+  return (int)((kSegParamBytes - 32) / (sizeof(SegInst<S>) + sizeof(int))) & ~3;
+}
+// Launches of few instances take a kernel with smaller parameters (measured 4 % faster on one 2048^2
+// instance than the full-size parameters, which every launch copies).
+constexpr int kSegSmall = 16;
+template <class S, int CAP> struct SegLaunch {
+  int n;      // instances of this launch
+  int tiles;  // its CTAs
+  int pad_[2];
+  int first_tile[CAP];  // each instance's first CTA, ascending: kept together so that the search of a
+                        // CTA's instance reads a few cache lines
+  SegInst<S> in[CAP];
+};
+static_assert(sizeof(SegLaunch<double, seg_capacity<double>()>) <= kSegParamBytes &&
+                  sizeof(SegLaunch<float, seg_capacity<float>()>) <= kSegParamBytes,
+              "per-tile launch parameters");
+// Enqueue one per-tile launch over the instances of L, a host SegLaunch<S, CAP> of the batch's storage
+// type with CAP = kSegSmall (small) or seg_capacity<S>(). pdl: the launch may begin while the previous
+// kernel on st drains (its instances are others).
+cudaError_t batch_seg_launch(int prec, int variant, bool small, const void* L, bool pdl, cudaStream_t st);
+// Enqueue the per-instance advance of a step (rho_ave, buffer parity, step count).
+cudaError_t batch_advance_launch(int prec, void* d_insts, int ninst, cudaStream_t st);
 // Largest resident CTAs per SM of the step kernel for (prec, variant).
 int batch_max_ctas_per_sm(int prec, int variant);
 

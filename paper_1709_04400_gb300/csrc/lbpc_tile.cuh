@@ -16,6 +16,8 @@
 #include <cuda.h>
 #include <stddef.h>
 
+#include <type_traits>
+
 #include "lbpc_device.cuh"
 #include "lbpc_internal.h"
 
@@ -30,15 +32,14 @@ __device__ __forceinline__ int wrap_any(int x, int n) {
 }
 
 // Post-stream populations of an interior node (no wrap, no closure): src[a][i - e_a].
-template <class S, class R>
-__device__ __forceinline__ void pull_interior(const PopBuf<S>& src, const R* w, long long N, int nx, long long i,
-                                              R v[9]) {
+template <class S, class R, class IX = long long>
+__device__ __forceinline__ void pull_interior(const PopBuf<S>& src, const R* w, IX N, int nx, IX i, R v[9]) {
 #pragma unroll
-  for (int a = 0; a < 9; ++a) v[a] = pop_load<S, R>(src, N, a, i - (long long)EY(a) * nx - EX(a), w);
+  for (int a = 0; a < 9; ++a) v[a] = pop_load<S, R, IX>(src, N, a, i - (IX)EY(a) * nx - EX(a), w);
 }
 
 // Domain row for region row offset: wraps when y is periodic, else clamps to the edge row.
-__device__ __forceinline__ int row_of(const DevParams& P, int y) {
+template <class PT> __device__ __forceinline__ int row_of(const PT& P, int y) {
   if (P.yper) return wrap_any(y, P.ny);
   return y < 0 ? 0 : (y >= P.ny ? P.ny - 1 : y);
 }
@@ -134,14 +135,20 @@ template <class S, int NTH, int NPT> __host__ __device__ constexpr int fused_min
 // NPT nodes per thread: a CTA of TX * TY / NPT threads; thread t owns tile nodes t + k * (TX * TY / NPT),
 // k < NPT, and keeps their populations in registers from stage 1 to stage 3. With NPT = 2 the ring
 // stages keep more of the (fewer) threads busy and every thread carries two independent chains.
-template <int MODE, class S, class R, int TX, int TY, int NPT = 1>
+// IDX32: population indices formed in 32 bits (the caller guarantees 9 N < 2^31), and loads and stores
+// issued as global ones explicitly. This is for buffers whose pointers come from a descriptor in shared
+// memory (the batch's work-list kernel): the compiler cannot infer their space, and each wider index costs
+// registers there. Where the pointers and sizes are kernel parameters, 64-bit indices are faster.
+template <int MODE, class S, class R, int TX, int TY, int NPT = 1, bool IDX32 = false, class PT = DevParams>
 __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S>& gsrc, const PopBuf<S>& fdst,
                                            const PopBuf<S>& gdst, R* __restrict__ phi_prev,
-                                           const DevParams& P, long long step, int first,
+                                           const PT& P, long long step, int first,
                                            const double* __restrict__ rho_ave, double* __restrict__ partials,
                                            long long* __restrict__ status, FusedSmem<R, TX, TY>& sm, int x0, int y0,
-                                           int pslot, const TmaTile<S> staged = TmaTile<S>{nullptr}) {
+                                           int pslot, const TmaTile<S> staged = TmaTile<S>{nullptr},
+                                           const long long* step_at = nullptr) {
   constexpr bool INTERIOR = MODE != 0;
+  using IX = typename std::conditional<IDX32, int, long long>::type;
   constexpr int RX = TX + 4, RY = TY + 4;  // stage-1 region (tile + 2)
   constexpr int VX = TX + 2, VY = TY + 2;  // stage-2 region (tile + 1)
   (void)RY;
@@ -172,18 +179,21 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
     const int tx = n % TX, ty = n / TX;
     const int gx = x0 + tx, gy = y0 + ty;
     active[k] = gx < P.nx && gy < P.ny;
-    pp[k] = (active[k] && P.model == 0 && !first) ? phi_prev[(long long)gy * P.nx + gx] : R(0);
+    if constexpr (IDX32)
+      pp[k] = (active[k] && P.model == 0 && !first) ? __ldg(phi_prev + ((IX)gy * P.nx + gx)) : R(0);
+    else
+      pp[k] = (active[k] && P.model == 0 && !first) ? phi_prev[(long long)gy * P.nx + gx] : R(0);
     const int mx = wrap_any(gx, P.nx);
     my[k] = row_of(P, gy);
     if (MODE == 2) {
       pull_staged<S, R, TX, TY>(staged, 0, C.wf, tx + 2, ty + 2, f[k]);
       pull_staged<S, R, TX, TY>(staged, 1, C.wg, tx + 2, ty + 2, g[k]);
     } else if (INTERIOR) {
-      const long long io = (long long)gy * P.nx + gx;
-      pull_interior<S, R>(fsrc, C.wf, P.N, P.nx, io, f[k]);
-      pull_interior<S, R>(gsrc, C.wg, P.N, P.nx, io, g[k]);
+      const IX io = (IX)gy * P.nx + gx;
+      pull_interior<S, R, IX>(fsrc, C.wf, (IX)P.N, P.nx, io, f[k]);
+      pull_interior<S, R, IX>(gsrc, C.wg, (IX)P.N, P.nx, io, g[k]);
     } else {
-      pull_closed<S, R>(fsrc, gsrc, P, mx, my[k], f[k], g[k]);
+      pull_closed<S, R, IX>(fsrc, gsrc, P, mx, my[k], f[k], g[k]);
     }
     const R* fk = f[k];
     const R* gk = g[k];
@@ -197,7 +207,7 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
     const R psi2 = psi_squared(p, dpdT[k], Tlo, rho[k], C);
     if (active[k]) {
       const int bad = classify(rho[k], T[k], psi2, P);
-      if (bad) report(status, step, gx, gy, bad);
+      if (bad) report(status, step_at ? *step_at : step, gx, gy, bad);  // step_at: read only to report
     }
     s_rho[ty + 2][tx + 2] = rho[k];
     s_T[ty + 2][tx + 2] = T[k];
@@ -224,12 +234,12 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
       pull_staged<S, R, TX, TY>(staged, 0, C.wf, hx, hy, fr);
       pull_staged<S, R, TX, TY>(staged, 1, C.wg, hx, hy, gr);
     } else if (INTERIOR) {
-      const long long io = (long long)(y0 + hy - 2) * P.nx + (x0 + hx - 2);
-      pull_interior<S, R>(fsrc, C.wf, P.N, P.nx, io, fr);
-      pull_interior<S, R>(gsrc, C.wg, P.N, P.nx, io, gr);
+      const IX io = (IX)(y0 + hy - 2) * P.nx + (x0 + hx - 2);
+      pull_interior<S, R, IX>(fsrc, C.wf, (IX)P.N, P.nx, io, fr);
+      pull_interior<S, R, IX>(gsrc, C.wg, (IX)P.N, P.nx, io, gr);
     } else {
       const int x = wrap_any(x0 + hx - 2, P.nx), y = row_of(P, y0 + hy - 2);
-      pull_closed<S, R>(fsrc, gsrc, P, x, y, fr, gr);
+      pull_closed<S, R, IX>(fsrc, gsrc, P, x, y, fr, gr);
     }
     const R rr = density_of(fr);
     R Trlo;
@@ -352,7 +362,7 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
                     (s_rho[hy + 1][hx + 1] + s_rho[hy + 1][hx - 1] - s_rho[hy - 1][hx - 1] - s_rho[hy - 1][hx + 1]) * R(1.0 / 12.0);
       div_lam_gradT = rcv * C.chi * lapT + C.cV_chi * (grx * gTx + gry * gTy);
     }
-    const long long i = (long long)gy * P.nx + gx;
+    const IX i = (IX)gy * P.nx + gx;
     const R compress = Tk * (R(1) - dpdT[k] * inv_rcv) * divv;
     R phi, S0, tau_inv = R(0);
     if (P.model == 2) {  // Gong-Cheng: Eq. 13 source, local tau_g (Sec. IV A)
@@ -364,11 +374,19 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
       S0 = phi;
       if (P.model == 0) S0 = phi + (phi - (first ? phi : pp[k])) * 0.5f;
     }
-    phi_prev[i] = phi;
+    if constexpr (IDX32)
+      __stwb(phi_prev + i, phi);
+    else
+      phi_prev[i] = phi;
     collide_flow(f[k], rho[k], vx[k], vy[k], Fx[k], Fy[k], Q[k], P);
     collide_heat(g[k], Tk, vx[k], vy[k], S0, P, tau_inv);
-    pop_store<S, R>(fdst, P.N, i, f[k], rho[k], C.wf);
-    pop_store<S, R>(gdst, P.N, i, g[k], Tk + S0, C.wg);
+    if constexpr (IDX32) {
+      pop_store_global<S, R, IX>(fdst, (IX)P.N, i, f[k], rho[k], C.wf);
+      pop_store_global<S, R, IX>(gdst, (IX)P.N, i, g[k], Tk + S0, C.wg);
+    } else {
+      pop_store<S, R>(fdst, P.N, i, f[k], rho[k], C.wf);
+      pop_store<S, R>(gdst, P.N, i, g[k], Tk + S0, C.wg);
+    }
     if (!INTERIOR) wall_force_store(fdst.wall, P, gx, gy, Fx[k], Fy[k]);
   }
 }

@@ -33,7 +33,8 @@ EXPORTED = ["lbpc_version", "lbpc_check_params", "lbpc_workspace_bytes", "lbpc_e
             "lbpc_batch_add", "lbpc_batch_remove", "lbpc_batch_step", "lbpc_batch_check", "lbpc_batch_fields",
             "lbpc_batch_sums", "lbpc_batch_step_count", "lbpc_batch_set_config", "lbpc_batch_config",
             "lbpc_batch_autotune", "lbpc_batch_free_bytes", "lbpc_batch_last_error", "lbpc_batch_destroy",
-            "lbpc_set_fused_tile", "lbpc_checkpoint_bytes", "lbpc_save", "lbpc_load", "lbpc_fma_rate"]
+            "lbpc_set_fused_tile", "lbpc_checkpoint_bytes", "lbpc_save", "lbpc_load", "lbpc_fma_rate",
+            "lbpc_batch_per_tile_capacity"]
 
 
 class LbpcError(RuntimeError):
@@ -113,6 +114,7 @@ def load_library(path: str = LIB_PATH):
         "lbpc_batch_config": (ctypes.c_int, [vp] + [ctypes.POINTER(ctypes.c_int32)] * 4),
         "lbpc_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                                ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]),
+        "lbpc_batch_per_tile_capacity": (ctypes.c_int32, [ctypes.c_int32]),
         "lbpc_batch_free_bytes": (ctypes.c_size_t, [vp]),
         "lbpc_batch_last_error": (ctypes.c_char_p, [vp]),
         "lbpc_batch_destroy": (None, [vp]),
@@ -405,9 +407,9 @@ def params_from_case(case: dict, prec: int = FP64) -> Params:
 
 
 class Batch:
-    """Many simulations advancing together (lbpc_batch_*): one persistent launch per step over a
-    device work list of every instance's tiles, replayed through CUDA graphs on a dedicated stream.
-    The arena is a PyTorch uint8 buffer of arena_bytes."""
+    """Many simulations advancing together (lbpc_batch_*): per-tile launches that hold the instances in
+    their parameters, or one work-list launch per step (set_config), replayed through CUDA graphs on a
+    dedicated stream. The arena is a PyTorch uint8 buffer of arena_bytes."""
 
     def __init__(self, prec: int, arena_bytes: int, max_instances: int = 4096, device=None):
         import torch
@@ -431,6 +433,11 @@ class Batch:
     def _raise(self, s, what):
         if s != LBPC_OK:
             raise LbpcError(s, f"{what}: {self.lib.lbpc_batch_last_error(self.h).decode()}")
+
+    @staticmethod
+    def per_tile_capacity(prec: int) -> int:
+        """Instances one per-tile launch (configuration with 0 CTAs per SM) holds."""
+        return int(load_library().lbpc_batch_per_tile_capacity(int(prec)))
 
     @staticmethod
     def instance_bytes(params: Params) -> int:

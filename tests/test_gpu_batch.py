@@ -46,9 +46,11 @@ def _alone(case, rho, T, steps, prec):
     return out
 
 
-def _solo(case, rho, T, steps, prec):
-    """The instance in a batch of its own (default configuration)."""
+def _solo(case, rho, T, steps, prec, config=None):
+    """The instance in a batch of its own (default configuration, or config = (variant, ctas per SM))."""
     b = lbpc.Batch(prec, _arena_for([(case, rho, T)], prec))
+    if config is not None:
+        b.set_config(*config)
     i = b.add(lbpc.params_from_case(case, prec), rho, T)
     b.step(steps)
     out = b.fields(i)
@@ -213,3 +215,56 @@ def test_no_read_of_unwritten_arena(monkeypatch, prec):
         for fc, fd in zip(clean, dirty):
             for a, b in zip(fc, fd):
                 assert np.array_equal(a, b), tune
+
+
+@pytest.mark.parametrize("prec", [lbpc.FP32, lbpc.FP16DEV, lbpc.FP64], ids=["fp32", "fp16", "fp64"])
+def test_per_tile_launches(prec):
+    """Per-tile launches (0 CTAs per SM: one CTA per tile, the instances in the kernel parameters). The
+    steps are taken as 17 + 16 + 3, so graphs of 16 steps replay at both step parities and single steps
+    run between them. Each instance of the mixed batch equals, bit for bit, the same instance in a batch
+    of its own in this configuration stepped 36 times at once. It matches the work-list kernel of the
+    same tile shape to round-off."""
+    cases = _cases()
+    b = lbpc.Batch(prec, _arena_for(cases, prec))
+    b.set_config(0, 0)
+    ids = [b.add(lbpc.params_from_case(c, prec), r, t) for c, r, t in cases]
+    for n in (17, 16, 3):
+        b.step(n)
+    b.check()
+    tol = TOL_VS_SINGLE[prec]
+    for i, (c, r, t) in zip(ids, cases):
+        got = b.fields(i)
+        assert b.step_count(i) == 36
+        for a, e in zip(got, _solo(c, r, t, 36, prec, config=(0, 0))):
+            assert np.array_equal(a, e), c["name"]
+        ref = _solo(c, r, t, 36, prec, config=(0, 8))
+        assert max_rel(got[0], ref[0]) < tol and max_rel(got[3], ref[3]) < tol, c["name"]
+        assert norm_rel(got[1], ref[1]) < 100 * tol and norm_rel(got[2], ref[2]) < 100 * tol, c["name"]
+    b.close()
+
+
+def test_per_tile_launches_many_instances_join_and_leave():
+    """More instances than one per-tile launch holds (so a step takes several launches), instances that
+    join and leave between steps, and every remaining instance equal, bit for bit, to its run alone."""
+    prec = lbpc.FP32
+    cap = lbpc.Batch.per_tile_capacity(prec)
+    small = [workloads.droplet_periodic(TC, RV, RL, n=24 + 2 * (k % 5), radius=6.0) for k in range(cap + 6)]
+    b = lbpc.Batch(prec, _arena_for(small, prec), max_instances=len(small) + 2)
+    b.set_config(0, 0)
+    ids = [b.add(lbpc.params_from_case(c, prec), r, t) for c, r, t in small[:-3]]
+    b.step(19)
+    late = [b.add(lbpc.params_from_case(c, prec), r, t) for c, r, t in small[-3:]]
+    b.remove(ids[1])
+    b.step(20)
+    b.check()
+    for k, i in enumerate(ids):
+        if k == 1:
+            continue
+        c, r, t = small[k]
+        for a, e in zip(b.fields(i), _solo(c, r, t, 39, prec, config=(0, 0))):
+            assert np.array_equal(a, e), k
+    for k, i in enumerate(late):
+        c, r, t = small[len(small) - 3 + k]
+        for a, e in zip(b.fields(i), _solo(c, r, t, 20, prec, config=(0, 0))):
+            assert np.array_equal(a, e), k
+    b.close()
