@@ -248,9 +248,10 @@ def _dtypes():
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels this bench
-# reports, from one-pass ncu captures of the same commands, keyed by (kernel, workload, storage). Each
-# entry carries the hash of the kernel sources it was captured on (kernel_source_hash); when the
-# sources differ from that hash the entry describes another build and the line reports null.
+# reports, from one-pass ncu captures of the same commands, keyed by (kernel, workload, storage); for
+# the batch's per-tile launches, the sum over the launches of one step. Each entry carries the hash of
+# the kernel sources it was captured on (kernel_source_hash); when the sources differ from that hash
+# the entry describes another build and the line reports null.
 MEASURED_TRAFFIC = {
     # one-pass ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of the bench's own commands
     ("k_collide", "droplet_evaporation_2048_dT0.1Tc", "fp64"): (1_539_759_360, "223ae50df45d436b"),
@@ -408,6 +409,11 @@ def batch_measure(lbpc, workloads, prec, instances, steps, warmup, variant=-1, c
     value = nodes * steps / batch_s / 1e6
     plain = nodes * steps / plain_s / 1e6
     peak_bw = _peak_hbm()
+    # per-tile launches (0 CTAs per SM): ceil(instances / capacity) launches and the advance per step;
+    # the work-list kernel: one launch and the advance
+    per_tile = cfg["ctas_per_sm"] == 0
+    kernel = "k_batch_tiles" if per_tile else "k_batch_step"
+    launches_per_step = (-(-len(insts) // lbpc.Batch.per_tile_capacity(prec)) + 1) if per_tile else 2
     bpn = storage_bytes_per_node(prec, lbpc)
     achieved = bpn * nodes / (batch_s / steps) / 1e9
     prec_name = {lbpc.FP64: "fp64", lbpc.FP32: "fp32", lbpc.FP16DEV: "fp16"}[prec]
@@ -419,11 +425,12 @@ def batch_measure(lbpc, workloads, prec, instances, steps, warmup, variant=-1, c
         "plain_path": {"value": plain, "unit": "MLUPS", "ms_per_step": plain_s * 1e3 / steps,
                        "how": "each instance stepped alone through lbpc_step (fused kernel, one launch per step)"},
         "batched_over_plain": value / plain,
-        "hbm": {"kernel": "k_batch_step", "bytes_per_node": bpn, "achieved": achieved, "peak": peak_bw,
+        "hbm": {"kernel": kernel, "bytes_per_node": bpn, "achieved": achieved, "peak": peak_bw,
                 "unit": "GB/s", "frac": achieved / peak_bw, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
-                "traffic": measured_traffic("k_batch_step", wname, prec_name)},
+                "traffic": measured_traffic(kernel, wname, prec_name),
+                "traffic_per": "step (every launch of the step)" if per_tile else "launch"},
         "l2": "working set of %.1f GB exceeds L2" % (nodes * bpn / 1e9),
-        "launches": 2 * steps, "clocks": clk.summary() if clk else None,
+        "launches": launches_per_step * steps, "clocks": clk.summary() if clk else None,
     }
 
 
