@@ -254,11 +254,11 @@ def _dtypes():
 # the entry describes another build and the line reports null.
 MEASURED_TRAFFIC = {
     # one-pass ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of the bench's own commands
-    ("k_collide", "droplet_evaporation_2048_dT0.1Tc", "fp64"): (1_539_759_360, "223ae50df45d436b"),
-    ("k_collide", "droplet_evaporation_2048_dT0.1Tc", "df64"): (1_639_971_328, "223ae50df45d436b"),
-    ("k_fused", "droplet_evaporation_4096_dT0.1Tc", "fp32"): (2_503_880_192, "223ae50df45d436b"),
-    ("k_fused", "droplet_evaporation_4096_dT0.1Tc", "fp16"): (1_579_616_000, "223ae50df45d436b"),
-    ("k_batch_step", "batched_evaporation_256", "fp32"): (4_114_644_736, "223ae50df45d436b"),
+    ("k_collide", "droplet_evaporation_2048_dT0.1Tc", "fp64"): (1_540_092_416, "81d0d305df801b22"),
+    ("k_collide", "droplet_evaporation_2048_dT0.1Tc", "df64"): (1_640_252_160, "81d0d305df801b22"),
+    ("k_fused", "droplet_evaporation_4096_dT0.1Tc", "fp32"): (2_503_385_088, "81d0d305df801b22"),
+    ("k_fused", "droplet_evaporation_4096_dT0.1Tc", "fp16"): (1_579_806_976, "81d0d305df801b22"),
+    ("k_batch_tiles", "batched_evaporation_256", "fp32"): (3_893_592_832, "81d0d305df801b22"),  # one step: 5 launches
 }
 
 
