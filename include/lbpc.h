@@ -185,9 +185,11 @@ typedef enum { LBPC_PATH_AUTO = 0, LBPC_PATH_SPLIT = 1, LBPC_PATH_FUSED = 2 } lb
 lbpc_status lbpc_set_path(lbpc_ctx* c, int32_t path);
 
 /* Tile configuration of the fused step (LBPC_FP32 and LBPC_FP16DEV): 0 = 32 x 16 tiles, one node per
- * thread; 1 = 32 x 8, one node per thread (default: smaller shared-memory footprint, four CTAs per SM,
- * more halo recomputation); 2 = 32 x 16, two nodes per thread; 3 = 32 x 32, two nodes per thread (less
- * halo recomputation per node). All compute the same step. LBPC_EINVAL outside 0..3. */
+ * thread; 1 = 32 x 8, one node per thread (smaller shared-memory footprint, four CTAs per SM, more halo
+ * recomputation); 2 = 32 x 16, two nodes per thread; 3 = 32 x 32, two nodes per thread (less halo
+ * recomputation per node); 4 = 32 x 8 in persistent CTAs that take tiles in order and start each next
+ * tile's staging copy while they finish the current tile (default). Where the rows are not 16-byte
+ * multiples (no staging), 4 runs as 1. All compute the same step. LBPC_EINVAL outside 0..4. */
 lbpc_status lbpc_set_fused_tile(lbpc_ctx* c, int32_t tile);
 
 /* Synchronise the stream and check the device status word. */

@@ -442,7 +442,7 @@ LBPC_API lbpc_status lbpc_set_path(lbpc_ctx* c, int32_t path) {
 }
 
 LBPC_API lbpc_status lbpc_set_fused_tile(lbpc_ctx* c, int32_t tile) {
-  if (!c || tile < 0 || tile > 3) return LBPC_EINVAL;
+  if (!c || tile < 0 || tile > 4) return LBPC_EINVAL;
   c->buf.fused_tile = tile;
   for (int k = 0; k < 2; ++k) {
     c->buf.tma[k] = nullptr;

@@ -41,9 +41,10 @@ struct alignas(64) TmaMaps {
 // holds at least this many; on narrow domains (nx < 4) it exceeds the 2 * ceil(N / 64) of the split step.
 inline size_t fused_max_tiles(int nx, int ny) { return (size_t)((nx + 31) / 32) * (size_t)((ny + 7) / 8); }
 
-// Fused-step tile configuration a new context starts with: 32 x 8 tiles, one node per thread (the
-// fastest measured on GB300 at 2048^2 - 4096^2 in FP32 and FP16).
-constexpr int kDefaultFusedTile = 1;
+// Fused-step tile configuration a new context starts with: 32 x 8 tiles, one node per thread, in
+// persistent CTAs that stage each next tile early (the fastest measured on GB300 at 2048^2 - 8192^2 in
+// FP32 and FP16).
+constexpr int kDefaultFusedTile = 4;
 
 // Device buffers of a context, carved from the caller's workspace.
 struct SplitBuffers {
@@ -56,7 +57,7 @@ struct SplitBuffers {
   void* planes[16];  // scratch planes of the split kernels, arithmetic type
   double* partials;  // per-block (split) or per-tile (fused) partial sums: max(2 * nblocks, fused_max_tiles)
   double* scalars;   // [0] rho_ave, [1] mass, [2] heat
-  long long* status; // [0] flag, [1] step, [2] x, [3] y, [4] code
+  long long* status; // [0] flag, [1] step, [2] x, [3] y, [4] code; [6] tile tickets of the persistent fused step
   const TmaMaps* tma[2] = {nullptr, nullptr};  // tensor maps of buffer A / B for the TMA-staged fused step
   int fused_tile = 1;  // 0: 32x16, 1: 32x8, 2: 32x16 two nodes per thread, 3: 32x32 two per thread (maps match)
 };

@@ -139,14 +139,22 @@ template <class S, int NTH, int NPT> __host__ __device__ constexpr int fused_min
 // issued as global ones explicitly. This is for buffers whose pointers come from a descriptor in shared
 // memory (the batch's work-list kernel): the compiler cannot infer their space, and each wider index costs
 // registers there. Where the pointers and sizes are kernel parameters, 64-bit indices are faster.
-template <int MODE, class S, class R, int TX, int TY, int NPT = 1, bool IDX32 = false, class PT = DevParams>
+// after_stage1: called by every thread once the tile has finished reading its staged populations (after
+// the block barrier that closes stage 1); the persistent TMA kernel starts the next tile's copy there.
+struct NoStageHook {
+  __device__ __forceinline__ void operator()() const {}
+};
+
+template <int MODE, class S, class R, int TX, int TY, int NPT = 1, bool IDX32 = false, class PT = DevParams,
+          class AfterStage1 = NoStageHook>
 __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S>& gsrc, const PopBuf<S>& fdst,
                                            const PopBuf<S>& gdst, R* __restrict__ phi_prev,
                                            const PT& P, long long step, int first,
                                            const double* __restrict__ rho_ave, double* __restrict__ partials,
                                            long long* __restrict__ status, FusedSmem<R, TX, TY>& sm, int x0, int y0,
                                            int pslot, const TmaTile<S> staged = TmaTile<S>{nullptr},
-                                           const long long* step_at = nullptr) {
+                                           const long long* step_at = nullptr,
+                                           AfterStage1 after_stage1 = AfterStage1{}) {
   constexpr bool INTERIOR = MODE != 0;
   using IX = typename std::conditional<IDX32, int, long long>::type;
   constexpr int RX = TX + 4, RY = TY + 4;  // stage-1 region (tile + 2)
@@ -262,6 +270,7 @@ __device__ __forceinline__ void fused_body(const PopBuf<S>& fsrc, const PopBuf<S
   } else {
     __syncthreads();
   }
+  after_stage1();
 
   // ---- stage 2: F and v on tile + 1 ----
   // F at stage-2 position (vx_, vy_) of the domain node (x, y); the stencil rows come from the clamped

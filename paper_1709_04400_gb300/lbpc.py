@@ -295,7 +295,8 @@ class Simulation:
         self._raise(self.lib.lbpc_set_path(self.ctx, int(path)), "lbpc_set_path")
 
     def set_fused_tile(self, tile):
-        """Tile shape of the fused step: 0 = 32 x 16, 1 = 32 x 8."""
+        """Tile configuration of the fused step (lbpc_set_fused_tile): 0 = 32 x 16, 1 = 32 x 8, 2 / 3 = 32 x 16 /
+        32 x 32 with two nodes per thread, 4 = 32 x 8 in persistent CTAs staging ahead (default)."""
         self._raise(self.lib.lbpc_set_fused_tile(self.ctx, int(tile)), "lbpc_set_fused_tile")
 
     def step(self, n=1, sync=True):

@@ -321,9 +321,32 @@ def test_fp16_deviation_storage(path):
 
 
 @pytest.mark.parametrize("prec", [lbpc.FP32, lbpc.FP16DEV], ids=["fp32", "fp16"])
+def test_persistent_staged_walk_matches(prec):
+    """Tile configuration 4 (persistent CTAs, each staging its next tile while it finishes the current
+    one) equals configuration 1 bit for bit on grids where it runs persistent (more than 8 tiles per
+    resident CTA). The grids are a 2048^2 droplet (16384 tiles, about 27 per CTA, edge tiles on the held
+    ring) and a 1024 x 2048 pool with walls, a pressure top, a heated strip and the domain-mean buoyancy
+    (8192 tiles, so the per-tile partial sums of rho come from CTAs that own several tiles)."""
+    for case, rho, T in (workloads.droplet_evaporation(TC, RV, RL, n=2048, radius=400.0, dT_ratio=0.1),
+                         workloads.mixed_small(TC, RV, RL, nx=1024, ny=2048)):
+        out = []
+        for tile in (1, 4):
+            sim = lbpc.Simulation(lbpc.params_from_case(case, prec))
+            sim.set_fused_tile(tile)
+            sim.init(rho, T)
+            sim.step(12)
+            sim.check()
+            out.append(sim.fields())
+            sim.close()
+        for a, b in zip(out[1], out[0]):
+            assert np.array_equal(a, b), case["name"]
+
+
+@pytest.mark.parametrize("prec", [lbpc.FP32, lbpc.FP16DEV], ids=["fp32", "fp16"])
 def test_fused_tile_shapes(prec):
     """Every tile configuration of the fused step (32 x 16 and 32 x 8 with one node per thread, 32 x 16
-    and 32 x 32 with two; TMA-staged interior tiles) computes the same step; the FP32 result stays
+    and 32 x 32 with two, 32 x 8 in persistent CTAs that stage each next tile early; TMA-staged interior
+    tiles) computes the same step; the FP32 result stays
     within 1e-4 of the oracle. A ragged 101 x 75 grid exercises partial tiles and the plain-load path
     (its rows are not 16-byte multiples, so no TMA).
 
@@ -335,14 +358,14 @@ def test_fused_tile_shapes(prec):
     between = 5e-5 if prec == lbpc.FP32 else 3e-4
     for case, rho, T in (workloads.droplet_periodic(TC, RV, RL), workloads.mixed_small(TC, RV, RL, nx=101, ny=75)):
         out = []
-        for tile in (0, 1, 2, 3):
+        for tile in (0, 1, 2, 3, 4):
             sim = lbpc.Simulation(lbpc.params_from_case(case, prec))
             sim.set_fused_tile(tile)
             sim.init(rho, T)
             sim.step(60)
             out.append(sim.fields())
             sim.close()
-        for same in ((0, 1), (2, 3)):  # same nodes per thread: the same bits
+        for same in ((0, 1), (0, 4), (2, 3)):  # same nodes per thread: the same bits
             for a, b in zip(out[same[1]], out[same[0]]):
                 assert np.array_equal(a, b), (case["name"], same)
         for a, b in zip(out[2], out[0]):
