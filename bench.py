@@ -254,11 +254,11 @@ def _dtypes():
 # the entry describes another build and the line reports null.
 MEASURED_TRAFFIC = {
     # one-pass ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of the bench's own commands
-    ("k_collide", "droplet_evaporation_2048_dT0.1Tc", "fp64"): (1_539_850_752, "1a646f4652076788"),
-    ("k_collide", "droplet_evaporation_2048_dT0.1Tc", "df64"): (1_639_954_944, "1a646f4652076788"),
-    ("k_fused", "droplet_evaporation_4096_dT0.1Tc", "fp32"): (2_502_697_472, "1a646f4652076788"),
-    ("k_fused", "droplet_evaporation_4096_dT0.1Tc", "fp16"): (1_578_365_952, "1a646f4652076788"),
-    ("k_batch_tiles", "batched_evaporation_256", "fp32"): (3_893_414_144, "1a646f4652076788"),  # one step: 5 launches
+    ("k_collide", "droplet_evaporation_2048_dT0.1Tc", "fp64"): (1_539_444_224, "51ee3432028044b0"),
+    ("k_collide", "droplet_evaporation_2048_dT0.1Tc", "df64"): (1_640_148_224, "51ee3432028044b0"),
+    ("k_fused", "droplet_evaporation_4096_dT0.1Tc", "fp32"): (2_502_832_640, "51ee3432028044b0"),
+    ("k_fused", "droplet_evaporation_4096_dT0.1Tc", "fp16"): (1_576_405_248, "51ee3432028044b0"),
+    ("k_batch_tiles", "batched_evaporation_256", "fp32"): (3_894_301_184, "51ee3432028044b0"),  # one step: 5 launches
 }
 
 

@@ -105,7 +105,9 @@ __global__ void __launch_bounds__(TX* TY / NPT, fused_min_blocks<S, TX * TY / NP
                      unsigned long long* __restrict__ tickets, const __grid_constant__ TmaMaps maps) {
   using B = TmaBox<S, TX, TY>;
   __shared__ FusedSmem<R, TX, TY> sm;
-  __shared__ int s_tile, s_next, s_after;  // this tile, the next one (being staged), the one after
+  // walk state, double-buffered by iteration parity: this tile and the next one (being staged); thread 0
+  // fills the other slot during the tile, so one block barrier per tile orders both
+  __shared__ int s_tile[2], s_next[2];
   extern __shared__ __align__(128) unsigned char dyn[];
   uint64_t* bar = (uint64_t*)(dyn + B::BYTES - 128);
   const int ntx = (P.nx + TX - 1) / TX, ntiles = ntx * ((P.ny + TY - 1) / TY);
@@ -124,21 +126,23 @@ __global__ void __launch_bounds__(TX* TY / NPT, fused_min_blocks<S, TX * TY / NP
     const int t0 = take();
     int x0, y0;
     if (t0 < ntiles && origin(t0, x0, y0)) tma_issue_tile<S, TX, TY>(dyn, bar, maps, x0, y0);
-    s_tile = t0;
-    s_next = t0 < ntiles ? take() : ntiles;
+    s_tile[0] = t0;
+    s_next[0] = t0 < ntiles ? take() : ntiles;
   }
   __syncthreads();
-  unsigned parity = 0;
-  for (;;) {
-    const int tile = s_tile;
+  unsigned parity = 0;  // of the mbarrier phase awaited next
+  for (int it = 0;; it ^= 1) {
+    const int tile = s_tile[it];
     if (tile >= ntiles) break;
-    // thread 0 starts the copy of the next tile, if interior, and takes the tile after it
+    // thread 0 starts the copy of the next tile, if interior, and records it and the tile after it as
+    // the next iteration's walk state
     auto start_next = [&]() {
       if (threadIdx.x != 0) return;
-      const int next = s_next;
+      const int next = s_next[it];
       int nx0, ny0;
       if (next < ntiles && origin(next, nx0, ny0)) tma_issue_tile<S, TX, TY>(dyn, bar, maps, nx0, ny0);
-      s_after = next < ntiles ? take() : ntiles;
+      s_tile[it ^ 1] = next;
+      s_next[it ^ 1] = next < ntiles ? take() : ntiles;
     };
     int x0, y0;
     if (origin(tile, x0, y0)) {
@@ -155,12 +159,7 @@ __global__ void __launch_bounds__(TX* TY / NPT, fused_min_blocks<S, TX * TY / NP
       fused_body<0, S, R, TX, TY, NPT>(fsrc, gsrc, fdst, gdst, phi_prev, P, step, first, rho_ave, partials, status, sm,
                                        x0, y0, tile);
     }
-    __syncthreads();  // the tile body is done with the shared arrays; s_after has landed
-    if (threadIdx.x == 0) {
-      s_tile = s_next;
-      s_next = s_after;
-    }
-    __syncthreads();
+    __syncthreads();  // the tile body is done with the shared arrays; the next walk state has landed
   }
 }
 
@@ -198,22 +197,25 @@ static cudaError_t fused_impl(const SplitBuffers& b, const DevParams& P, int cur
       using B = TmaBox<S, TX, TY>;
       // The dynamic shared-memory limit is held per device context, so it is set before every launch:
       // the call is cheap, thread-safe, and right after a device reset or on a second device.
-      int resident = 0;  // CTAs of the persistent kernel that fit on the device at once (0: not used)
+      bool persistent = false;
       if constexpr (LOOP) {
         cudaError_t e = cudaFuncSetAttribute(k_fused_tma_loop<S, R, TX, TY, NPT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, B::BYTES);
         if (e != cudaSuccess) return e;
+        int resident = 0;  // CTAs of the persistent kernel that fit on the device at once
         if ((e = loop_residency<S, R, TX, TY, NPT>(B::BYTES, &resident)) != cudaSuccess) return e;
+        // persistent CTAs pay off where each walks many tiles (measured: +5 % to +12 % in FP32 from
+        // 2048^2, 27 or more per CTA; 1-8 % slower at 1024^2, 7 per CTA); smaller grids take one CTA per tile
+        if ((long long)grid.x * grid.y > 8LL * resident) {
+          unsigned long long* tickets = (unsigned long long*)(b.status + 6);
+          if ((e = cudaMemsetAsync(tickets, 0, sizeof *tickets, st)) != cudaSuccess) return e;
+          k_fused_tma_loop<S, R, TX, TY, NPT><<<resident, TX * TY / NPT, B::BYTES, st>>>(
+              fs, gs, fd, gd, (R*)b.phi_prev, P, step, step == 0, b.scalars, b.partials, b.status, tickets,
+              *b.tma[cur]);
+          persistent = true;
+        }
       }
-      // persistent CTAs pay off where each walks many tiles (measured: +5 % to +12 % in FP32 from 2048^2,
-      // where each walks 27 or more; 1-8 % slower at 1024^2, 7 per CTA); smaller grids take one CTA per tile
-      if (LOOP && (long long)grid.x * grid.y > 8LL * resident) {
-        unsigned long long* tickets = (unsigned long long*)(b.status + 6);
-        const cudaError_t e = cudaMemsetAsync(tickets, 0, sizeof *tickets, st);
-        if (e != cudaSuccess) return e;
-        k_fused_tma_loop<S, R, TX, TY, NPT><<<resident, TX * TY / NPT, B::BYTES, st>>>(
-            fs, gs, fd, gd, (R*)b.phi_prev, P, step, step == 0, b.scalars, b.partials, b.status, tickets, *b.tma[cur]);
-      } else {
+      if (!persistent) {
         const cudaError_t e =
             cudaFuncSetAttribute(k_fused_tma<S, R, TX, TY, NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, B::BYTES);
         if (e != cudaSuccess) return e;
