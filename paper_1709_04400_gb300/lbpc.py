@@ -412,7 +412,9 @@ class Batch:
     their parameters, or one work-list launch per step (set_config), replayed through CUDA graphs on a
     dedicated stream. The arena is a PyTorch uint8 buffer of arena_bytes."""
 
-    def __init__(self, prec: int, arena_bytes: int, max_instances: int = 4096, device=None):
+    def __init__(self, prec: int, arena_bytes: int, max_instances: int = 4096, device=None, high_priority=False):
+        """high_priority: the batch's stream takes the device's highest stream priority, so that its CTAs are
+        dispatched first when other work shares the GPU (a serving batch beside bulk simulations)."""
         import torch
 
         if not torch.cuda.is_available():
@@ -422,7 +424,8 @@ class Batch:
         self.prec = prec
         with torch.cuda.device(self.device):
             self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=self.device)
-            self.stream = torch.cuda.Stream(self.device)
+            prio = torch.cuda.Stream.priority_range()[1] if high_priority else 0
+            self.stream = torch.cuda.Stream(self.device, priority=prio)
         h = ctypes.c_void_p()
         s = self.lib.lbpc_batch_create(prec, max_instances, ctypes.c_void_p(self.arena.data_ptr()), int(arena_bytes),
                                        ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))

@@ -93,7 +93,8 @@ class Server:
     def __init__(self, prec=lbpc.FP32, hbm_budget_bytes=8 << 30, max_chunk=256, keep_fields=False,
                  max_instances=4096, clock=time.perf_counter):
         self.prec = prec
-        self.batch = lbpc.Batch(prec, hbm_budget_bytes, max_instances=max_instances)
+        # the served requests wait on their results: their stream goes before bulk work on the same GPU
+        self.batch = lbpc.Batch(prec, hbm_budget_bytes, max_instances=max_instances, high_priority=True)
         p0 = lbpc.Params(nx=8, ny=8)
         self.Tc, _ = lbpc.eos_critical(p0)
         self.rho_v, self.rho_l, _ = lbpc.coexistence(p0, 0.86 * self.Tc)

@@ -30,7 +30,7 @@ class FakeClock:
 class FakeBatch:
     instances = []  # every FakeBatch created, for inspection
 
-    def __init__(self, prec, arena_bytes, max_instances=4096, device=None):
+    def __init__(self, prec, arena_bytes, max_instances=4096, device=None, high_priority=False):
         self.budget = int(arena_bytes)
         self.used = {}
         self.steps = {}
