@@ -323,8 +323,8 @@ def test_fp16_deviation_storage(path):
 @pytest.mark.parametrize("prec", [lbpc.FP32, lbpc.FP16DEV], ids=["fp32", "fp16"])
 def test_persistent_staged_walk_matches(prec):
     """Tile configuration 4 (persistent CTAs, each staging its next tile while it finishes the current
-    one) equals configuration 1 bit for bit on grids where it runs persistent (more than 8 tiles per
-    resident CTA). The grids are a 2048^2 droplet (16384 tiles, about 27 per CTA, edge tiles on the held
+    one) equals configuration 1 bit for bit after 64 steps on grids where it runs persistent (more than 8
+    tiles per resident CTA). The grids are a 2048^2 droplet (16384 tiles, about 27 per CTA, edge tiles on the held
     ring) and a 1024 x 2048 pool with walls, a pressure top, a heated strip and the domain-mean buoyancy
     (8192 tiles, so the per-tile partial sums of rho come from CTAs that own several tiles)."""
     for case, rho, T in (workloads.droplet_evaporation(TC, RV, RL, n=2048, radius=400.0, dT_ratio=0.1),
@@ -334,7 +334,7 @@ def test_persistent_staged_walk_matches(prec):
             sim = lbpc.Simulation(lbpc.params_from_case(case, prec))
             sim.set_fused_tile(tile)
             sim.init(rho, T)
-            sim.step(12)
+            sim.step(64)
             sim.check()
             out.append(sim.fields())
             sim.close()
